@@ -1,0 +1,298 @@
+"""Benchmark: H^2 x H^2 products per second at block-relative eps = 1e-6.
+
+Workload (one step = one product C = A*B through h2_mul, inputs resident in
+HBM): 128 x 128 grid on the unit square (n = 16384), A = -log|x-y|/(2 pi)
+(diagonal 1), B = exp(-|x-y|^2/0.1), leaf size 64, eta 2, tensor Chebyshev
+order 4 (k = 16), FP64 throughout (the plain form; no other form exists yet).
+
+Prints one JSON line (rank 0).  Multi-GPU (torchrun): independent replicas,
+one per GPU, no collective on the data path ("scaling": "weak").
+
+--impl reference times the CPU oracle (numpy FP64, single thread, spawned
+process) on the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "H²×H² products/s at block-rel eps=1e-6, chosen vs plain FP64 form; p50/p99 ms"
+UNIT = "products/s"
+GRID = 128
+EPS = 1e-6
+KIND_NAMES = ["k_gemm", "k_copy", "k_qr", "k_qapply", "k_svd", "k_scan", "k_finalize"]
+
+
+def workload_config():
+    return {
+        "workload": f"grid2d_n{GRID * GRID}: C=A*B, A=-log|x-y|/(2pi) diag 1, B=exp(-|x-y|^2/0.1), "
+                    f"leaf 64, eta 2, Chebyshev order 4 (k=16), eps={EPS:g}",
+        "n": GRID * GRID, "k": 16, "leaf_size": 64, "eta": 2.0, "eps": EPS, "form": "plain FP64",
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+def fp64_peak():
+    """FP64 ALU peak of the part: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x max SM clock."""
+    mhz = 2070.0
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        mhz = float(peaks.get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_subprocess(grid, eps, nprod):
+    """Time `nprod` oracle products (build excluded) in a spawned single-thread process."""
+    code = (
+        "import sys, time, json\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from oracle import h2oracle as O\n"
+        "from paper_2403_01566_gb300 import inputs as I\n"
+        f"w = I.grid_2d({grid}, {eps!r})\n"
+        "X = O.build_h2(w.points, w.kernel_a.kind, w.kernel_a.kparam(), w.eta, w.leaf_size, w.order)\n"
+        "Y = O.build_h2(w.points, w.kernel_b.kind, w.kernel_b.kparam(), w.eta, w.leaf_size, w.order, tree=X.rows)\n"
+        "ts = []\n"
+        f"for _ in range({nprod}):\n"
+        "    t0 = time.perf_counter(); O.multiply(X, Y, w.eps); ts.append(time.perf_counter() - t0)\n"
+        "print(json.dumps(ts))\n")
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    # warm-up on a small grid, then one full product per timed step budget
+    oracle_subprocess(16, EPS, 1)
+    nprod = 1
+    ts = oracle_subprocess(GRID, EPS, nprod)
+    value = nprod / sum(ts)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": nprod,
+        "warmup": 1, "ms_per_step": 1e3 * sum(ts) / nprod, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{nprod} full product(s) of the workload on one host thread "
+                                   "(numpy FP64 oracle, input build excluded); warm-up on a 16x16 grid"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+
+    from paper_2403_01566_gb300 import h2
+    from paper_2403_01566_gb300 import inputs as I
+
+    w = I.grid_2d(GRID, EPS)
+    A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
+    B = h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up (plan build, graph capture, pool growth)
+    for _ in range(max(args.warmup, 3)):
+        h2.mul(A, B, EPS, stream=sptr)
+    torch.cuda.synchronize()
+
+    # timed steps: device time per product with CUDA events on the product's stream
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    outs = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        outs.append(h2.mul(A, B, EPS, sync=False, stream=sptr))
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    if dist is not None:
+        dist.barrier()
+    for C in outs:
+        C.check()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    launches = outs[0].info().launches * args.steps
+    st0 = outs[0].info()
+    for C in outs:
+        C.free()
+    outs.clear()
+
+    # end to end through the public API: points from pinned host memory ->
+    # h2_build (A, B) -> h2_mul -> C x read back to the host, per step.
+    pts_pinned = torch.from_numpy(np.ascontiguousarray(w.points)).pin_memory()
+    x = np.ascontiguousarray(I.random_vector(w.n, 1))
+    e2e_steps = max(2, min(5, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        p = pts_pinned.numpy()
+        Ae = h2.build(p, w.kernel_a, w.eta, w.leaf_size, w.order)
+        Be = h2.build(p, w.kernel_b, w.eta, w.leaf_size, w.order)
+        Ce = h2.mul(Ae, Be, EPS, stream=sptr)
+        y = Ce.matvec(x)
+        Ce.free()
+        Ae.free()
+        Be.free()
+    torch.cuda.synchronize()
+    e2e_value = e2e_steps / (time.perf_counter() - t0)
+    assert np.isfinite(y).all()
+
+    # roofline of the dominant kernel: one profiled product (stages one by one)
+    prof = (h2.KernelProf * 7)()
+    Cp = h2.mul_profile(A, B, EPS, prof, stream=sptr)
+    Cp.free()
+    kinds = [(KIND_NAMES[i], prof[i]) for i in range(7)]
+    prof_total = sum(p.ms for _, p in kinds)
+    dom_name, dom = max(kinds, key=lambda kv: kv[1].ms)
+    peak = fp64_peak()
+    achieved = dom.flops / (dom.ms / 1e3) / 1e12 if dom.ms > 0 else 0.0
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = tr.get(dom_name)
+    except Exception:
+        pass
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ts = oracle_subprocess(GRID, EPS, 1)
+        cpu = {"value": 1.0 / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one full product of the workload on one host thread (numpy FP64 oracle, "
+                         "input build excluded)"}
+
+    if rank == 0:
+        pcts = sorted(step_ms)
+        p50 = statistics.median(pcts)
+        p99 = pcts[min(len(pcts) - 1, int(math.ceil(0.99 * len(pcts))) - 1)]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(), parallelism=f"replicas x{world}"),
+            "p50_ms": p50, "p99_ms": p99, "wall_s": t_wall,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(2 * w.points.nbytes + x.nbytes), "d2h_bytes_per_step": int(x.nbytes),
+                    "what": "h2_build(A), h2_build(B) from pinned host points, h2_mul, C x read back"},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
+                         "peak_source": "FP64 ALU peak derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                         "share": dom.ms / prof_total if prof_total else None},
+            "kernels": {nm: {"launches": p.launches, "jobs": p.jobs, "ms": round(p.ms, 4),
+                             "gflop": round(p.flops / 1e9, 4), "gb": round(p.bytes / 1e9, 4)} for nm, p in kinds},
+            "product": {"nadm": st0.nadm, "ninadm": st0.ninadm, "agglomerated": st0.nagglomerated,
+                        "rank_max": max(st0.row_rank_max, st0.col_rank_max), "workspace_gb": st0.workspace_bytes / 1e9},
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

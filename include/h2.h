@@ -1,0 +1,168 @@
+/*
+ * h2.h -- C ABI of the GB300 (sm_103a) library for adaptive H^2-matrix
+ * multiplication with block-relative error control.
+ *
+ * Method: S. Boerm, "Adaptive multiplication of H^2-matrices with
+ * block-relative error control" (arXiv 2403.01566).  Given H^2-matrices
+ * X (I x J) and Y (J x K) that share the cluster tree of J, h2_mul builds an
+ * H^2-matrix C ~ X*Y with adaptively chosen isometric cluster bases such that
+ * every admissible block b of C satisfies
+ *     ||C_b - (XY)_b||_2 <= eps * ||(XY)_b||_2            (Sections 5.1-5.3)
+ * and every inadmissible block is exact up to rounding.
+ *
+ * Conventions for every entry point:
+ *   - All matrices handled by the library are FP64.
+ *   - Vectors and dense matrices exchanged with the caller are in the caller's
+ *     ORIGINAL point ordering; the library permutes internally.
+ *   - Dense matrices are column-major n x n.
+ *   - Handles are opaque, owned by the library, device resident, and released
+ *     only by h2_free.  Inputs are never modified; one handle may be used by
+ *     several concurrent h2_mul / h2_matvec calls.
+ *   - Every call returns 0 (H2_OK) or a negative error code; no exception
+ *     crosses the ABI.  A failed call leaves any output handle set to NULL.
+ *   - All device work of a call runs on opts->stream when given, else on the
+ *     library's own stream; calls with sync = 1 return after the work is done.
+ */
+#ifndef H2_GB300_H
+#define H2_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define H2_OK 0
+#define H2_EINVAL (-1)    /* invalid argument (n <= 0, dim not in 1..3, eps < 0, NaN, ...) */
+#define H2_ETREE (-2)     /* X's column cluster tree differs from Y's row cluster tree */
+#define H2_ENOMEM (-3)    /* device or host allocation failed */
+#define H2_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define H2_ENOCONV (-5)   /* a Jacobi SVD hit its sweep cap without converging */
+#define H2_ECUDA (-6)     /* a CUDA runtime call failed (see h2_last_cuda_error) */
+#define H2_ERANK (-7)     /* an adaptive rank exceeded h2_mul_opts.max_rank */
+#define H2_ENOTREADY (-8) /* no CUDA device is available */
+
+/* Kernel functions g(x,y) of the Nystroem matrices (Section 6 stand-ins):
+ * kparam = {scale, diagonal value (entry i == j), width, unused}. */
+#define H2_KERNEL_LOG 0   /* -scale * log|x-y|            */
+#define H2_KERNEL_INV 1   /*  scale / |x-y|               */
+#define H2_KERNEL_GAUSS 2 /*  scale * exp(-|x-y|^2/width) */
+#define H2_KERNEL_EXP 3   /*  scale * exp(-|x-y|/width)   */
+
+typedef struct h2_matrix h2_matrix;
+
+/* Parameters of h2_build (Section 2).
+ *   eta        admissibility  max(diam Omega_t, diam Omega_s) <= eta * dist(Omega_t, Omega_s)
+ *              (eq. (2) of the paper with eta = 2*eta_paper), eta > 0
+ *   leaf_size  maximal cluster size of a leaf, >= 2
+ *   order      Chebyshev points per axis (eq. (3)); rank k = order^dim, 1..8
+ *   kernel     H2_KERNEL_*;  kparam as above
+ *   dim        spatial dimension of the points, 1..3 */
+typedef struct {
+  double eta;
+  int leaf_size;
+  int order;
+  int kernel;
+  double kparam[4];
+  int dim;
+} h2_build_opts;
+
+/* Parameters of h2_mul (Sections 5.1-5.3).
+ *   theta      weight factor of the block-relative error control, 0 < theta < 1/2
+ *              (binary trees); 0 selects 1/4
+ *   max_rank   cap on the adaptive ranks (storage padding of C), <= 64; 0 selects
+ *              min(64, max(32, 2k))
+ *   precision  0 = FP64 throughout (the only value accepted by this version)
+ *   sync       1 = return after the product is complete and report device errors;
+ *              0 = return after enqueueing (errors are reported by h2_check)
+ *   stream     cudaStream_t to run on, or NULL for the library stream */
+typedef struct {
+  double theta;
+  int max_rank;
+  int precision;
+  int sync;
+  void* stream;
+} h2_mul_opts;
+
+typedef struct {
+  int64_t n;
+  int dim;
+  int depth;          /* leaves are on level `depth` */
+  int nclusters;      /* clusters per tree */
+  int nadm;           /* admissible leaves of the block tree */
+  int ninadm;         /* inadmissible leaves */
+  int kpad;           /* padded rank used for storage */
+  int row_rank_min, row_rank_max, col_rank_min, col_rank_max;
+  int nagglomerated;  /* admissible blocks of a product that needed agglomeration */
+  int64_t device_bytes;
+  int launches;       /* kernel launches of the product that made this matrix (0 for inputs) */
+  int64_t workspace_bytes; /* device workspace of that product */
+} h2_stats;
+
+/* Build the H^2 approximation of the Nystroem matrix g(x_i, x_j) on `points`
+ * (row-major n x dim, host memory, copied) by cardinality-balanced bisection
+ * cluster trees, the admissibility block tree and tensor Chebyshev
+ * interpolation (Def. 1-4, eq. (2)-(5)).  Row and column trees/bases coincide. */
+int h2_build(const double* points, int64_t n, const h2_build_opts* opts, h2_matrix** out);
+
+/* C ~ A*B with block-relative error eps in every admissible block (Sections 3-5).
+ * A's column cluster tree must equal B's row cluster tree (H2_ETREE).
+ * eps = 0 keeps every singular value (exact product up to rounding).
+ * The result is a new handle; C's block tree is the admissibility block tree of
+ * (A's row tree, B's column tree) with A's eta. */
+int h2_mul(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts,
+           h2_matrix** C);
+
+/* Measurement helper (not part of the method): per kernel kind, the launches,
+ * summed device time (CUDA events around every stage on the product's stream)
+ * and the algorithmic work of one product computed like h2_mul.  Kinds:
+ * 0 batched GEMM, 1 copy, 2 Householder QR, 3 Q application, 4 Jacobi SVD,
+ * 5 rank prefix sums, 6 finalize.  flops count the FP64 operations of the
+ * algorithm with the ranks the device decided (Householder QR 2mn^2 - 2n^3/3,
+ * one-sided Jacobi 6 m n (n-1) per executed sweep); bytes are the algorithmic
+ * reads and writes of each job.  The stages run one by one (no graph).
+ * `out` must hold H2_PROFILE_KINDS entries.  The product is returned in *C. */
+#define H2_PROFILE_KINDS 7
+typedef struct {
+  int launches;
+  int jobs;
+  double ms;
+  double flops;
+  double bytes;
+} h2_kernel_prof;
+
+int h2_mul_profile(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts,
+                   h2_kernel_prof* out, h2_matrix** C);
+
+/* Device error state of a product computed with sync = 0 (waits for it). */
+int h2_check(const h2_matrix* C);
+
+/* y = A x.  x, y of length n (caller ordering); on_device = 1: both are device
+ * pointers, else host pointers.  Runs on the library stream and synchronizes. */
+int h2_matvec(const h2_matrix* A, const double* x, double* y, int on_device);
+
+/* Dense n x n column-major expansion (caller ordering) into `out` (host or device). */
+int h2_to_dense(const h2_matrix* A, double* out, int on_device);
+
+/* Statistics; synchronizes. */
+int h2_info(const h2_matrix* A, h2_stats* out);
+
+/* Ranks of the row and column cluster bases per cluster, clusters in level
+ * order (root first, children in order); each array holds nclusters ints. */
+int h2_ranks(const h2_matrix* A, int* row_ranks, int* col_ranks);
+
+/* Cluster-order permutation: perm[i] = original index of the i-th point. */
+int h2_permutation(const h2_matrix* A, int64_t* perm);
+
+void h2_free(h2_matrix* A);
+
+const char* h2_strerror(int code);
+
+/* Text of the last CUDA error seen by the library (thread local). */
+const char* h2_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2_GB300_H */

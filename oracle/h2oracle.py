@@ -203,7 +203,11 @@ def descendants_at(c, level):
 
 
 def diam(c):
-    return math.sqrt(sum((float(c.hi[a]) - float(c.lo[a])) ** 2 for a in range(len(c.lo))))
+    acc = 0.0
+    for a in range(len(c.lo)):
+        g = float(c.hi[a]) - float(c.lo[a])
+        acc += g * g
+    return math.sqrt(acc)
 
 
 def dist(t, s):

@@ -1,0 +1,718 @@
+// C ABI of the library (include/h2.h): handle management, device upload of
+// the inputs, and execution of the planned stage lists on the GPU.
+//
+// A product plan is built once per (X, Y, options) and cached in X; its stage
+// list is captured into a CUDA graph on first use and replayed afterwards.
+// The graph reads every pointer from a per-plan device control block
+// (ExecCtx), which is rewritten before each replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/h2.h"
+#include "h2_build.h"
+#include "h2_internal.h"
+#include "h2_kernels.h"
+#include "h2_plan.h"
+
+namespace h2 {
+
+static thread_local std::string g_last_cuda;
+
+static int cuda_fail(cudaError_t e, const char* where) {
+  g_last_cuda = std::string(where) + ": " + cudaGetErrorString(e);
+  return H2_ECUDA;
+}
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static std::mutex g_init_mu;
+static bool g_inited = false;
+static cudaStream_t g_stream = nullptr;
+static uint64_t g_uid = 0;
+
+static int lib_init() {
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (g_inited) return H2_OK;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return H2_ENOTREADY;
+  CK(kernels_init());
+  CK(cudaStreamCreateWithFlags(&g_stream, cudaStreamNonBlocking));
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  g_inited = true;
+  return H2_OK;
+}
+
+// --------------------------------------------------- plan device state ----
+struct PlanRT {
+  std::shared_ptr<Plan> plan;
+  void* d_blob = nullptr;      // job arrays + slot init + idx + konst + rank_src
+  DeviceJobs dj;
+  int* d_slot_init = nullptr;
+  int* d_idx = nullptr;
+  double* d_konst = nullptr;
+  int* d_rank_src = nullptr;
+  char* d_ctrl = nullptr;      // ExecCtx, scal, nrm, slots, err
+  ExecCtx* d_ctx = nullptr;
+  double* d_scal = nullptr;
+  double* d_nrm = nullptr;
+  int* d_slot = nullptr;
+  int* d_err = nullptr;
+  double* d_ws = nullptr;
+  size_t svd_smem = 0;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t last = nullptr;  // completion of the last replay (workspace reuse)
+  int nrank = 0;
+  // pinned ring of control headers (asynchronous upload without a host wait)
+  static constexpr int RING = 64;
+  static constexpr int HDR = 1024;
+  char* h_ring = nullptr;
+  cudaEvent_t ring_ev[RING] = {};
+  int ring_next = 0;
+  ~PlanRT() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (last) cudaEventDestroy(last);
+    for (auto& e : ring_ev)
+      if (e) cudaEventDestroy(e);
+    if (h_ring) cudaFreeHost(h_ring);
+    cudaFree(d_blob);
+    cudaFree(d_ctrl);
+    cudaFree(d_ws);
+  }
+};
+
+template <class T>
+static size_t put(std::vector<char>& blob, const std::vector<T>& v) {
+  size_t off = (blob.size() + 255) & ~size_t(255);
+  blob.resize(off + v.size() * sizeof(T));
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+static int upload_plan(PlanRT& rt, const std::vector<int>& rank_src) {
+  Plan& P = *rt.plan;
+  std::vector<char> blob;
+  const size_t o_go = put(blob, P.gout), o_gt = put(blob, P.gterm), o_cp = put(blob, P.copy), o_qr = put(blob, P.qr),
+               o_qa = put(blob, P.qap), o_sv = put(blob, P.svd), o_sc = put(blob, P.scan),
+               o_si = put(blob, P.slot_init), o_ix = put(blob, P.idx), o_k = put(blob, P.konst),
+               o_rs = put(blob, rank_src);
+  CK(cudaMalloc(&rt.d_blob, std::max<size_t>(blob.size(), 256)));
+  CK(cudaMemcpy(rt.d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  char* b = (char*)rt.d_blob;
+  rt.dj.gemm_out = (const GemmOut*)(b + o_go);
+  rt.dj.gemm_term = (const GemmTerm*)(b + o_gt);
+  rt.dj.copy = (const CopyJob*)(b + o_cp);
+  rt.dj.qr = (const QrJob*)(b + o_qr);
+  rt.dj.qapply = (const QApplyJob*)(b + o_qa);
+  rt.dj.svd = (const SvdJob*)(b + o_sv);
+  rt.dj.scan = (const ScanJob*)(b + o_sc);
+  rt.d_slot_init = (int*)(b + o_si);
+  rt.d_idx = (int*)(b + o_ix);
+  rt.d_konst = (double*)(b + o_k);
+  rt.d_rank_src = (int*)(b + o_rs);
+  rt.nrank = (int)rank_src.size();
+  const size_t nslot = std::max<size_t>(P.slot_init.size(), 1);
+  const size_t sz = 512 + 16 * (size_t)P.nscal + 4 * nslot + 64;
+  CK(cudaMalloc(&rt.d_ctrl, sz));
+  rt.d_ctx = (ExecCtx*)rt.d_ctrl;
+  rt.d_scal = (double*)(rt.d_ctrl + 512);
+  rt.d_nrm = rt.d_scal + P.nscal;
+  rt.d_slot = (int*)(rt.d_nrm + P.nscal);
+  rt.d_err = rt.d_slot + nslot;
+  CK(cudaMalloc(&rt.d_ws, std::max<int64_t>(P.ws_len, 1) * sizeof(double)));
+  rt.svd_smem = svd_smem_bytes(P.svd_maxrows, P.svd_maxcols);
+  CK(cudaEventCreateWithFlags(&rt.last, cudaEventDisableTiming));
+  return H2_OK;
+}
+
+// Writes the control block (ExecCtx + parameters) through a pinned ring slot.
+static int enqueue_header(PlanRT& rt, const ExecCtx& ctx, const double* params, cudaStream_t s) {
+  if (!rt.h_ring) {
+    CK(cudaMallocHost(&rt.h_ring, (size_t)PlanRT::RING * PlanRT::HDR));
+    for (auto& e : rt.ring_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  const int slot = rt.ring_next;
+  rt.ring_next = (rt.ring_next + 1) % PlanRT::RING;
+  CK(cudaEventSynchronize(rt.ring_ev[slot]));  // previous use of this slot has been copied
+  char* h = rt.h_ring + (size_t)slot * PlanRT::HDR;
+  std::memset(h, 0, 512 + sizeof(double) * PARAM_COUNT);
+  std::memcpy(h, &ctx, sizeof(ctx));
+  for (int i = 0; i < PARAM_COUNT; ++i) std::memcpy(h + 512 + 8 * i, &params[i], 8);
+  CK(cudaStreamWaitEvent(s, rt.last, 0));
+  CK(cudaMemcpyAsync(rt.d_ctrl, h, 512 + sizeof(double) * PARAM_COUNT, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(rt.ring_ev[slot], s));
+  return H2_OK;
+}
+
+// Enqueue one execution of the plan on stream s (graph replay when captured).
+static int run_plan(PlanRT& rt, double* bx, double* by, double* bc, int* out_int, const double* params,
+                    cudaStream_t s, bool use_graph) {
+  Plan& P = *rt.plan;
+  ExecCtx ctx{};
+  ctx.base[AR_WS] = rt.d_ws;
+  ctx.base[AR_X] = bx;
+  ctx.base[AR_Y] = by;
+  ctx.base[AR_C] = bc;
+  ctx.base[AR_K] = rt.d_konst;
+  ctx.slot = rt.d_slot;
+  ctx.scal = rt.d_scal;
+  ctx.nrm = rt.d_nrm;
+  ctx.err = rt.d_err;
+  ctx.idx = rt.d_idx;
+  ctx.out_int = out_int;
+  ctx.rank_src = rt.d_rank_src;
+  ctx.nrank = out_int ? rt.nrank : 0;
+  // header: ExecCtx then the parameters at scal[0..PARAM_COUNT)
+  {
+    int rc = enqueue_header(rt, ctx, params, s);
+    if (rc) return rc;
+  }
+  if (use_graph && !rt.graph) {
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(rt.d_slot, rt.d_slot_init, sizeof(int) * P.slot_init.size(), cudaMemcpyDeviceToDevice, cs);
+    cudaMemsetAsync(rt.d_err, 0, sizeof(int), cs);
+    for (const Stage& st : P.stages) launch_stage(st, rt.d_ctx, rt.dj, rt.svd_smem, cs);
+    launch_finalize(rt.d_ctx, rt.nrank, cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "capture");
+    e = cudaGraphInstantiate(&rt.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate");
+  }
+  if (use_graph) {
+    CK(cudaGraphLaunch(rt.graph, s));
+  } else {
+    if (!P.slot_init.empty())
+      CK(cudaMemcpyAsync(rt.d_slot, rt.d_slot_init, sizeof(int) * P.slot_init.size(), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(rt.d_err, 0, sizeof(int), s));
+    for (const Stage& st : P.stages) launch_stage(st, rt.d_ctx, rt.dj, rt.svd_smem, s);
+    launch_finalize(rt.d_ctx, rt.nrank, s);
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(rt.last, s));
+  return H2_OK;
+}
+
+// Stage-by-stage execution with CUDA events; per kernel kind: launches, jobs,
+// device time and the algorithmic work with the ranks the device decided.
+static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int* out_int, const double* params,
+                             cudaStream_t s, h2_kernel_prof* prof) {
+  Plan& P = *rt.plan;
+  int* d_sweeps = nullptr;
+  CK(cudaMalloc(&d_sweeps, sizeof(int) * std::max<size_t>(P.svd.size(), 1)));
+  CK(cudaMemset(d_sweeps, 0, sizeof(int) * std::max<size_t>(P.svd.size(), 1)));
+  ExecCtx ctx{};
+  ctx.base[AR_WS] = rt.d_ws;
+  ctx.base[AR_X] = bx;
+  ctx.base[AR_Y] = by;
+  ctx.base[AR_C] = bc;
+  ctx.base[AR_K] = rt.d_konst;
+  ctx.slot = rt.d_slot;
+  ctx.scal = rt.d_scal;
+  ctx.nrm = rt.d_nrm;
+  ctx.err = rt.d_err;
+  ctx.idx = rt.d_idx;
+  ctx.out_int = out_int;
+  ctx.rank_src = rt.d_rank_src;
+  ctx.nrank = out_int ? rt.nrank : 0;
+  ctx.svd_sweeps = d_sweeps;
+  {
+    int rc = enqueue_header(rt, ctx, params, s);
+    if (rc) return rc;
+  }
+  if (!P.slot_init.empty())
+    CK(cudaMemcpyAsync(rt.d_slot, rt.d_slot_init, sizeof(int) * P.slot_init.size(), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(rt.d_err, 0, sizeof(int), s));
+  const size_t ns = P.stages.size();
+  std::vector<cudaEvent_t> ev(2 * ns + 2);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (size_t i = 0; i < ns; ++i) {
+    CK(cudaEventRecord(ev[2 * i], s));
+    launch_stage(P.stages[i], rt.d_ctx, rt.dj, rt.svd_smem, s);
+    CK(cudaEventRecord(ev[2 * i + 1], s));
+  }
+  CK(cudaEventRecord(ev[2 * ns], s));
+  launch_finalize(rt.d_ctx, rt.nrank, s);
+  CK(cudaEventRecord(ev[2 * ns + 1], s));
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(rt.last, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int> slot(P.slot_init.size()), sweeps(P.svd.size());
+  if (!slot.empty()) CK(cudaMemcpy(slot.data(), rt.d_slot, slot.size() * 4, cudaMemcpyDeviceToHost));
+  if (!sweeps.empty()) CK(cudaMemcpy(sweeps.data(), d_sweeps, sweeps.size() * 4, cudaMemcpyDeviceToHost));
+  cudaFree(d_sweeps);
+  auto dv = [&](const Dim& d) {
+    int v = d.c;
+    if (d.s1 >= 0) v += slot[d.s1];
+    if (d.s2 >= 0) v += slot[d.s2];
+    return (double)v;
+  };
+  for (int k = 0; k < H2_PROFILE_KINDS; ++k) prof[k] = h2_kernel_prof{0, 0, 0.0, 0.0, 0.0};
+  for (size_t i = 0; i <= ns; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+    const int kind = i < ns ? P.stages[i].kind : 6;
+    h2_kernel_prof& pr = prof[kind];
+    pr.launches += 1;
+    pr.ms += ms;
+    if (i == ns) continue;
+    const Stage& st = P.stages[i];
+    pr.jobs += st.count;
+    for (int j = 0; j < st.count; ++j) {
+      double fl = 0, by = 0;
+      const int64_t J = st.first + j;
+      switch (st.kind) {
+        case ST_GEMM: {
+          const GemmOut& O = P.gout[J];
+          const double m = dv(O.m), n = O.clampn ? std::min(dv(O.n), 64.0) : dv(O.n);
+          if (m <= 0 || n <= 0) break;
+          by += 8 * m * n * (O.beta ? 2 : 1);
+          for (int t = O.t0; t < O.t1; ++t) {
+            const GemmTerm& T = P.gterm[t];
+            if (T.b.arena < 0) {
+              fl += m * n;
+              by += 8 * m * n;
+            } else if (T.c.arena < 0) {
+              const double k1 = dv(T.k1);
+              fl += 2 * m * n * k1;
+              by += 8 * (m * k1 + k1 * n);
+            } else {
+              const double k1 = dv(T.k1), k2 = dv(T.k2);
+              fl += 2 * m * k1 * k2 + 2 * m * k2 * n;
+              by += 8 * (m * k1 + k1 * k2 + k2 * n);
+            }
+          }
+          break;
+        }
+        case ST_COPY: {
+          const CopyJob& C = P.copy[J];
+          const double r = dv(C.rows), c = dv(C.cols);
+          by += 8 * (r * c + std::max(r, dv(C.zrows)) * std::max(c, dv(C.zcols)));
+          break;
+        }
+        case ST_QR: {
+          const QrJob& Q = P.qr[J];
+          const double r = dv(Q.rows), c = dv(Q.cols);
+          fl += r >= c ? 2 * r * c * c - 2 * c * c * c / 3 : 2 * c * r * r - 2 * r * r * r / 3;
+          by += 16 * r * c;
+          break;
+        }
+        case ST_QAPPLY: {
+          const QApplyJob& Q = P.qap[J];
+          const double r = dv(Q.rows), q = std::min(dv(Q.q), dv(Q.rows)), nc = dv(Q.ncols);
+          fl += std::max(0.0, 4 * r * q * nc - 2 * q * q * nc);
+          by += 8 * (r * q + 2 * r * nc);
+          break;
+        }
+        case ST_SVD: {
+          const SvdJob& S = P.svd[J];
+          const double r = dv(S.rows), c = dv(S.cols);
+          fl += 6 * r * c * (c - 1) * sweeps[J] + 2 * r * c;
+          by += 16 * r * c;
+          break;
+        }
+        default:
+          break;
+      }
+      pr.flops += fl;
+      pr.bytes += by;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return H2_OK;
+}
+
+static int map_err(int dev_err) {
+  switch (dev_err) {
+    case 0: return H2_OK;
+    case -5: return H2_ENOCONV;
+    case -7: return H2_ERANK;
+    default: return H2_EINVAL;
+  }
+}
+
+static MatDesc desc_of(const h2_matrix* A) {
+  MatDesc d;
+  d.rows = A->rows.get();
+  d.cols = A->cols.get();
+  d.blocks = A->blocks.get();
+  d.k = A->kpad;
+  d.off_V = A->off_V;
+  d.off_E = A->off_E;
+  d.off_W = A->off_W;
+  d.off_F = A->off_F;
+  d.off_S = A->off_S;
+  d.off_N = A->off_N;
+  d.off_VF = A->off_VF;
+  d.off_WF = A->off_WF;
+  return d;
+}
+
+// Explicit level bases of a matrix (needed when it is a factor or expanded).
+static int ensure_level_bases(h2_matrix* A, cudaStream_t s) {
+  if (A->levels_ready) return H2_OK;
+  const double params[PARAM_COUNT] = {0.0, 0.0};
+  {
+    PlanRT rt;
+    rt.plan = make_levelbasis_plan(*A->rows, A->kpad, AR_X, A->off_V, A->off_E, A->off_VF);
+    int rc = upload_plan(rt, {});
+    if (rc) return rc;
+    rc = run_plan(rt, A->d_arena, nullptr, nullptr, nullptr, params, s, false);
+    if (rc) return rc;
+    if (!A->same_basis) {
+      PlanRT rt2;
+      rt2.plan = make_levelbasis_plan(*A->cols, A->kpad, AR_X, A->off_W, A->off_F, A->off_WF);
+      rc = upload_plan(rt2, {});
+      if (rc) return rc;
+      rc = run_plan(rt2, A->d_arena, nullptr, nullptr, nullptr, params, s, false);
+      if (rc) return rc;
+      CK(cudaStreamSynchronize(s));
+    }
+    CK(cudaStreamSynchronize(s));
+  }
+  A->levels_ready = true;
+  return H2_OK;
+}
+
+}  // namespace h2
+
+using namespace h2;
+
+extern "C" {
+
+const char* h2_strerror(int code) {
+  switch (code) {
+    case H2_OK: return "ok";
+    case H2_EINVAL: return "invalid argument";
+    case H2_ETREE: return "column cluster tree of A differs from the row cluster tree of B";
+    case H2_ENOMEM: return "out of memory";
+    case H2_ETIMEOUT: return "device wait timed out";
+    case H2_ENOCONV: return "Jacobi SVD did not converge";
+    case H2_ECUDA: return "CUDA error";
+    case H2_ERANK: return "adaptive rank above max_rank";
+    case H2_ENOTREADY: return "no CUDA device";
+    default: return "unknown error";
+  }
+}
+
+const char* h2_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+int h2_build(const double* points, int64_t n, const h2_build_opts* o, h2_matrix** out) {
+  if (!out) return H2_EINVAL;
+  *out = nullptr;
+  if (!points || !o || n <= 0 || n > (int64_t)1 << 30 || o->dim < 1 || o->dim > 3 || o->leaf_size < 2 ||
+      o->order < 1 || o->order > 8 || !(o->eta > 0) || o->kernel < 0 || o->kernel > 3)
+    return H2_EINVAL;
+  for (int64_t i = 0; i < n * o->dim; ++i)
+    if (!std::isfinite(points[i])) return H2_EINVAL;
+  int k = 1;
+  for (int a = 0; a < o->dim; ++a) k *= o->order;
+  if (k > GEMM_MAXTILE || o->leaf_size > SVD_MAXDIM) return H2_EINVAL;
+  int rc = lib_init();
+  if (rc) return rc;
+  auto A = new h2_matrix();
+  try {
+    A->dim = o->dim;
+    A->eta = o->eta;
+    A->kpad = k;
+    A->rows = std::make_shared<Tree>();
+    build_cluster_tree(points, n, o->dim, o->leaf_size, *A->rows);
+    A->cols = A->rows;
+    A->blocks = std::make_shared<BlockTree>();
+    build_block_tree(*A->rows, *A->cols, o->eta, *A->blocks);
+    HostH2 H;
+    assemble_chebyshev(points, *A->rows, *A->blocks, o->order, o->kernel, o->kparam, H);
+    const Tree& T = *A->rows;
+    A->same_basis = true;
+    A->off_V = 0;
+    A->off_E = A->off_V + (int64_t)H.V.size();
+    A->off_S = A->off_E + (int64_t)H.E.size();
+    A->off_N = A->off_S + (int64_t)H.S.size();
+    A->off_VF = A->off_N + (int64_t)H.N.size();
+    A->off_W = A->off_V;
+    A->off_F = A->off_E;
+    A->off_WF = A->off_VF;
+    A->arena_len = A->off_VF + (int64_t)(T.depth + 1) * T.n * k;
+    if (cudaMalloc(&A->d_arena, A->arena_len * sizeof(double)) != cudaSuccess) {
+      delete A;
+      return H2_ENOMEM;
+    }
+    cudaMemcpy(A->d_arena + A->off_V, H.V.data(), H.V.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(A->d_arena + A->off_E, H.E.data(), H.E.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(A->d_arena + A->off_S, H.S.data(), H.S.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(A->d_arena + A->off_N, H.N.data(), H.N.size() * 8, cudaMemcpyHostToDevice);
+    std::vector<int> ints(2 * T.ncl + 1, k);
+    ints[2 * T.ncl] = 0;
+    cudaMalloc(&A->d_int, ints.size() * sizeof(int));
+    cudaMemcpy(A->d_int, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice);
+    A->uid = ++g_uid;
+    rc = ensure_level_bases(A, g_stream);
+    if (rc) {
+      h2_free(A);
+      return rc;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      h2_free(A);
+      return cuda_fail(e, "h2_build");
+    }
+  } catch (...) {
+    delete A;
+    return H2_EINVAL;
+  }
+  *out = A;
+  return H2_OK;
+}
+
+void h2_free(h2_matrix* A) {
+  if (!A) return;
+  if (A->done) {
+    cudaEventSynchronize(A->done);
+    cudaEventDestroy(A->done);
+  }
+  A->plans.clear();
+  if (A->d_arena) cudaFree(A->d_arena);
+  if (A->d_int) cudaFree(A->d_int);
+  delete A;
+}
+
+static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts, h2_kernel_prof* prof,
+                    h2_matrix** Cout) {
+  if (!Cout) return H2_EINVAL;
+  *Cout = nullptr;
+  if (!Ac || !Bc || !(eps >= 0.0) || !std::isfinite(eps)) return H2_EINVAL;
+  h2_matrix* A = const_cast<h2_matrix*>(Ac);
+  h2_matrix* B = const_cast<h2_matrix*>(Bc);
+  if (A->cols->hash != B->rows->hash || A->cols->n != B->rows->n) return H2_ETREE;
+  if (A->kpad != B->kpad) return H2_EINVAL;
+  double theta = (opts && opts->theta > 0.0) ? opts->theta : 0.25;
+  if (!(theta < 0.5)) return H2_EINVAL;
+  const int max_rank = opts ? opts->max_rank : 0;
+  if (opts && opts->precision != 0) return H2_EINVAL;
+  if (max_rank < 0 || max_rank > GEMM_MAXTILE) return H2_EINVAL;
+  const bool sync = opts ? opts->sync != 0 : true;
+  cudaStream_t s = (opts && opts->stream) ? (cudaStream_t)opts->stream : g_stream;
+  int rc = lib_init();
+  if (rc) return rc;
+  if ((rc = ensure_level_bases(A, s)) || (rc = ensure_level_bases(B, s))) return rc;
+  // plan (cached in A)
+  std::shared_ptr<PlanRT> rt;
+  {
+    std::lock_guard<std::mutex> lk(A->mu);
+    auto key = std::make_pair((const h2_matrix*)B, max_rank * 1000 + (int)std::lround(theta * 997.0));
+    auto it = A->plans.find(key);
+    if (it != A->plans.end() && it->second->uid_b == B->uid) {
+      rt = std::static_pointer_cast<PlanRT>(it->second->rt);
+    } else {
+      MulOptions mo;
+      mo.eta = A->eta;
+      mo.theta = theta;
+      mo.max_rank = max_rank;
+      std::shared_ptr<Plan> plan;
+      try {
+        plan = make_product_plan(desc_of(A), desc_of(B), mo);
+      } catch (const std::exception& ex) {
+        g_last_cuda = ex.what();
+        return H2_EINVAL;
+      }
+      rt = std::make_shared<PlanRT>();
+      rt->plan = plan;
+      std::vector<int> rank_src;
+      rank_src.insert(rank_src.end(), plan->rank_row_slot.begin(), plan->rank_row_slot.end());
+      rank_src.insert(rank_src.end(), plan->rank_col_slot.begin(), plan->rank_col_slot.end());
+      rc = upload_plan(*rt, rank_src);
+      if (rc) return rc;
+      auto entry = std::make_shared<PlanEntry>();
+      entry->rt = rt;
+      entry->uid_b = B->uid;
+      A->plans[key] = entry;
+    }
+  }
+  Plan& P = *rt->plan;
+  auto C = new h2_matrix();
+  C->dim = A->dim;
+  C->eta = A->eta;
+  C->kpad = P.kpad;
+  C->rows = A->rows;
+  C->cols = B->cols;
+  C->blocks = P.cblocks;
+  C->same_basis = false;
+  C->off_V = P.c_off_V;
+  C->off_E = P.c_off_E;
+  C->off_W = P.c_off_W;
+  C->off_F = P.c_off_F;
+  C->off_S = P.c_off_S;
+  C->off_N = P.c_off_N;
+  C->off_VF = P.c_len;
+  C->off_WF = C->off_VF + (int64_t)(C->rows->depth + 1) * C->rows->n * P.kpad;
+  C->arena_len = C->off_WF + (int64_t)(C->cols->depth + 1) * C->cols->n * P.kpad;
+  C->nagglomerated = P.nagg;
+  C->launches = (int)P.stages.size() + 1;
+  C->workspace_bytes = P.ws_len * 8;
+  C->uid = ++g_uid;
+  C->stream = s;
+  if (cudaMallocAsync(&C->d_arena, C->arena_len * sizeof(double), s) != cudaSuccess ||
+      cudaMallocAsync(&C->d_int, (2 * C->rows->ncl + 1) * sizeof(int), s) != cudaSuccess) {
+    delete C;
+    return H2_ENOMEM;
+  }
+  cudaMemsetAsync(C->d_arena, 0, P.c_len * sizeof(double), s);
+  const double params[PARAM_COUNT] = {eps / 4.0 * std::sqrt(1.0 - 2.0 * theta), eps / 3.0};
+  rc = prof ? run_plan_profiled(*rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, prof)
+            : run_plan(*rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, true);
+  if (rc) {
+    h2_free(C);
+    return rc;
+  }
+  cudaEventCreateWithFlags(&C->done, cudaEventDisableTiming);
+  cudaEventRecord(C->done, s);
+  *Cout = C;
+  if (sync) {
+    rc = h2_check(C);
+    if (rc) {
+      h2_free(C);
+      *Cout = nullptr;
+      return rc;
+    }
+  }
+  return H2_OK;
+}
+
+int h2_mul(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts, h2_matrix** C) {
+  return mul_impl(A, B, eps, opts, nullptr, C);
+}
+
+int h2_mul_profile(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts,
+                   h2_kernel_prof* out, h2_matrix** C) {
+  if (!out) return H2_EINVAL;
+  return mul_impl(A, B, eps, opts, out, C);
+}
+
+int h2_check(const h2_matrix* C) {
+  if (!C) return H2_EINVAL;
+  if (C->done) {
+    cudaError_t e = cudaEventSynchronize(C->done);
+    if (e != cudaSuccess) return cuda_fail(e, "h2_check");
+  }
+  int err = 0;
+  const int ncl = C->rows->ncl;
+  CK(cudaMemcpy(&err, C->d_int + 2 * ncl, sizeof(int), cudaMemcpyDeviceToHost));
+  return map_err(err);
+}
+
+int h2_ranks(const h2_matrix* A, int* rr, int* rc) {
+  if (!A || !rr || !rc) return H2_EINVAL;
+  if (A->done) cudaEventSynchronize(A->done);
+  const int ncl = A->rows->ncl;
+  CK(cudaMemcpy(rr, A->d_int, ncl * sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(rc, A->d_int + ncl, ncl * sizeof(int), cudaMemcpyDeviceToHost));
+  return H2_OK;
+}
+
+int h2_permutation(const h2_matrix* A, int64_t* perm) {
+  if (!A || !perm) return H2_EINVAL;
+  std::memcpy(perm, A->rows->perm.data(), sizeof(int64_t) * A->rows->n);
+  return H2_OK;
+}
+
+int h2_info(const h2_matrix* A, h2_stats* st) {
+  if (!A || !st) return H2_EINVAL;
+  std::memset(st, 0, sizeof(*st));
+  const int ncl = A->rows->ncl;
+  std::vector<int> rr(ncl), rc(ncl);
+  int r = h2_ranks(A, rr.data(), rc.data());
+  if (r) return r;
+  st->n = A->rows->n;
+  st->dim = A->dim;
+  st->depth = A->rows->depth;
+  st->nclusters = ncl;
+  st->nadm = (int)A->blocks->adm_list.size();
+  st->ninadm = (int)A->blocks->inadm_list.size();
+  st->kpad = A->kpad;
+  st->row_rank_min = *std::min_element(rr.begin(), rr.end());
+  st->row_rank_max = *std::max_element(rr.begin(), rr.end());
+  st->col_rank_min = *std::min_element(rc.begin(), rc.end());
+  st->col_rank_max = *std::max_element(rc.begin(), rc.end());
+  st->nagglomerated = A->nagglomerated;
+  st->device_bytes = A->arena_len * 8;
+  st->launches = A->launches;
+  st->workspace_bytes = A->workspace_bytes;
+  return H2_OK;
+}
+
+int h2_matvec(const h2_matrix* Ac, const double* x, double* y, int on_device) {
+  if (!Ac || !x || !y) return H2_EINVAL;
+  h2_matrix* A = const_cast<h2_matrix*>(Ac);
+  int rc = lib_init();
+  if (rc) return rc;
+  if (A->done) CK(cudaEventSynchronize(A->done));
+  cudaStream_t s = g_stream;
+  PlanRT rt;
+  rt.plan = make_matvec_plan(desc_of(A));
+  rc = upload_plan(rt, {});
+  if (rc) return rc;
+  const int nr = A->rows->n, nc = A->cols->n;
+  std::vector<double> xc(nc), yc(nr), xh(nc);
+  if (on_device) CK(cudaMemcpy(xh.data(), x, nc * 8, cudaMemcpyDeviceToHost));
+  else std::memcpy(xh.data(), x, nc * 8);
+  for (int i = 0; i < nc; ++i) xc[i] = xh[A->cols->perm[i]];
+  CK(cudaMemcpy(rt.d_ws, xc.data(), nc * 8, cudaMemcpyHostToDevice));
+  const double params[PARAM_COUNT] = {0.0, 0.0};
+  rc = run_plan(rt, A->d_arena, nullptr, nullptr, nullptr, params, s, false);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  // y lies after x in the workspace (offset rounded to 32 doubles)
+  const int64_t oy = ((int64_t)std::max(nc, 1) + 31) & ~int64_t(31);
+  CK(cudaMemcpy(yc.data(), rt.d_ws + oy, nr * 8, cudaMemcpyDeviceToHost));
+  std::vector<double> yo(nr);
+  for (int i = 0; i < nr; ++i) yo[A->rows->perm[i]] = yc[i];
+  if (on_device) CK(cudaMemcpy(y, yo.data(), nr * 8, cudaMemcpyHostToDevice));
+  else std::memcpy(y, yo.data(), nr * 8);
+  return H2_OK;
+}
+
+int h2_to_dense(const h2_matrix* Ac, double* out, int on_device) {
+  if (!Ac || !out) return H2_EINVAL;
+  h2_matrix* A = const_cast<h2_matrix*>(Ac);
+  int rc = lib_init();
+  if (rc) return rc;
+  if (A->done) CK(cudaEventSynchronize(A->done));
+  cudaStream_t s = g_stream;
+  if ((rc = ensure_level_bases(A, s))) return rc;
+  PlanRT rt;
+  rt.plan = make_dense_plan(desc_of(A));
+  rc = upload_plan(rt, {});
+  if (rc) return rc;
+  const double params[PARAM_COUNT] = {0.0, 0.0};
+  rc = run_plan(rt, A->d_arena, nullptr, nullptr, nullptr, params, s, false);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  const int64_t nr = A->rows->n, nc = A->cols->n;
+  std::vector<double> d((size_t)nr * nc), o((size_t)nr * nc);
+  CK(cudaMemcpy(d.data(), rt.d_ws, d.size() * 8, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < nr; ++i)
+    for (int64_t j = 0; j < nc; ++j) o[(size_t)A->cols->perm[j] * nr + A->rows->perm[i]] = d[(size_t)i * nc + j];
+  if (on_device) CK(cudaMemcpy(out, o.data(), o.size() * 8, cudaMemcpyHostToDevice));
+  else std::memcpy(out, o.data(), o.size() * 8);
+  return H2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Batched-operation descriptors shared by the host planner (h2_plan.cpp) and
+// the sm_103a kernels (h2_kernels.cu).
+//
+// A product is compiled on the host into a list of stages; every stage is one
+// kernel launch over a list of independent jobs of one kind (small GEMM chains,
+// strided copies, Householder QR, Q application, one-sided Jacobi SVD with a
+// rank decision, prefix sums of ranks).  Matrix sizes that the method decides
+// on the device (adaptive ranks) are "dims" that read integer slots written by
+// earlier stages, so the whole stage list is fixed per (X, Y) structure, runs
+// without host synchronisation and can be captured in one CUDA graph.
+//
+// All matrices are FP64.  Unless a job says otherwise a matrix is row-major:
+// element (i, j) of a matrix with leading dimension ld is at p[i*ld + j].
+#pragma once
+#include <stdint.h>
+
+namespace h2 {
+
+// AR_WS per-product workspace, AR_X / AR_Y the factors, AR_C the product,
+// AR_K constants of the plan (identity matrices).
+enum Arena : int { AR_WS = 0, AR_X = 1, AR_Y = 2, AR_C = 3, AR_K = 4, AR_NONE = -1, AR_COUNT = 5 };
+
+// value = c + slot[s1] + slot[s2] (s1/s2 < 0: absent)
+struct Dim {
+  int c, s1, s2;
+};
+
+// address = base[arena] + off + slot[ds] * dm + slot[ds2] * dm2  (ds < 0: absent)
+struct Ptr {
+  int64_t off;
+  int arena;
+  int ds, dm;
+  int ds2, dm2;
+};
+
+// out(m x n) = beta*out + sum_terms alpha * op(A)(m x k1) op(B)(k1 x k2) op(C)(k2 x n)
+// (two-factor term when c.arena < 0: op(A)(m x k1) op(B)(k1 x n);
+//  plain add when b.arena < 0: op(A)(m x n)).
+struct GemmOut {
+  Ptr o;
+  int ldo;
+  Dim m, n;
+  int beta;   // 0: overwrite, 1: accumulate
+  int t0, t1; // term range
+  int clampn; // 1: n = min(n, 64) (a wider output is covered by further tiles)
+};
+
+struct GemmTerm {
+  Ptr a, b, c;
+  int lda, ldb, ldc;
+  Dim k1, k2;
+  int ta, tb, tc;
+  double alpha;
+  int scale_idx;  // >= 0: alpha *= scal[scale_idx]
+};
+
+// dst(i,j) = alpha*scal*(trans ? src(j,i) : src(i,j)), i < rows, j < cols
+// (src.arena < 0: writes zeros).  Elements with rows <= i < zrows or
+// cols <= j < zcols are set to zero.
+struct CopyJob {
+  Ptr src, dst;
+  int lds, ldd;
+  Dim rows, cols;
+  Dim zrows, zcols;
+  int trans;
+  double alpha;
+  int scale_idx;
+};
+
+// In-place Householder QR of the COLUMN-major matrix a (rows x cols, leading
+// dimension lda): on exit the upper triangle holds R, the part below the
+// diagonal the reflectors v (v_0 = 1 implicit) and tau[j] the factors.
+// If r.arena >= 0 the cols x cols upper-triangular R is also written row-major
+// to r (ldr); rows i >= q = min(rows, cols) are zero.
+struct QrJob {
+  Ptr a, tau, r;
+  int lda, ldr;
+  Dim rows, cols;
+};
+
+// out(rows x ncols) = H_0 H_1 ... H_{q-1} [Y; 0]  with the reflectors of a QrJob
+// (Y is q x ncols row-major), i.e. the thin Q factor applied to Y.
+struct QApplyJob {
+  Ptr a, tau, y, out;
+  int lda, ldy, ldo;
+  Dim rows, q, ncols;
+};
+
+// One-sided Jacobi on the columns of M (rows x cols); M = src if !trans (src is
+// row-major rows x cols) else M = src^T (src row-major cols x rows).
+// Writes the singular values sorted descending (sig, cols entries), the left
+// singular vectors U (rows x cols row-major, column j = u_j, zero for sigma_j=0)
+// if u.arena >= 0, and a rank decision into slot[rank_slot]:
+//   mode 0: none, 1: count(sigma > tol), 2: count(sigma > tol*sigma_0),
+//   4: norm only (writes sigma_0 to nrm[norm_idx] and 1/sigma_0 (0 if
+//   sigma_0 == 0) to scal[norm_idx]).
+// The threshold is tol * scal[tol_idx] (tol alone if tol_idx < 0).
+// A rank above cap sets the error flag (H2_ERANK) and is clamped to cap.
+struct SvdJob {
+  Ptr src, u, sig;
+  int lds, ldu;
+  Dim rows, cols;
+  int trans;
+  int mode;
+  double tol;
+  int tol_idx;
+  int rank_slot;
+  int cap;
+  int norm_idx;
+};
+
+// slot[out + i] = sum_{j < i} slot[in[j]] for i = 0..count (count+1 outputs);
+// in[] lists slot indices (in the int index table at idx_off).
+struct ScanJob {
+  int idx_off;
+  int count;
+  int out;
+};
+
+enum StageKind : int { ST_GEMM = 0, ST_COPY = 1, ST_QR = 2, ST_QAPPLY = 3, ST_SVD = 4, ST_SCAN = 5 };
+
+struct Stage {
+  int kind;
+  int64_t first;  // first job index in the kind's job array
+  int count;      // number of jobs
+  int tag;        // phase id, for profiling
+};
+
+// Kernel parameters common to all stages.
+// It lives in device memory (one control block per plan) so that a captured
+// CUDA graph of the stage list can be replayed with new operand pointers.
+struct ExecCtx {
+  double* base[AR_COUNT];
+  int* slot;
+  double* scal;   // [0, PARAM_COUNT): parameters; then per-block 1/||G||
+  double* nrm;    // per-block ||G||
+  int* err;       // device error flag
+  const int* idx; // int index table (scan inputs)
+  int* out_int;   // product: ranks (rows, then columns) and error flag
+  const int* rank_src;
+  int nrank;
+  int pad;
+  int* svd_sweeps;  // per SVD job: sweeps executed (profiling)
+};
+
+}  // namespace h2

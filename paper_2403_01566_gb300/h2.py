@@ -1,0 +1,188 @@
+"""Thin ctypes binding of the C ABI declared in include/h2.h.
+
+Argument marshalling only: every step of the product runs in the CUDA library
+``lib/libh2gb300.so`` (built in-tree by ``__graft_entry__.build()``).  There is
+no CPU fallback; loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libh2gb300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "h2.h")
+
+H2_OK, H2_EINVAL, H2_ETREE, H2_ENOMEM, H2_ETIMEOUT, H2_ENOCONV, H2_ECUDA, H2_ERANK, H2_ENOTREADY = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("eta", C.c_double), ("leaf_size", C.c_int), ("order", C.c_int), ("kernel", C.c_int),
+                ("kparam", C.c_double * 4), ("dim", C.c_int)]
+
+
+class MulOpts(C.Structure):
+    _fields_ = [("theta", C.c_double), ("max_rank", C.c_int), ("precision", C.c_int), ("sync", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("dim", C.c_int), ("depth", C.c_int), ("nclusters", C.c_int),
+                ("nadm", C.c_int), ("ninadm", C.c_int), ("kpad", C.c_int), ("row_rank_min", C.c_int),
+                ("row_rank_max", C.c_int), ("col_rank_min", C.c_int), ("col_rank_max", C.c_int),
+                ("nagglomerated", C.c_int), ("device_bytes", C.c_int64), ("launches", C.c_int),
+                ("workspace_bytes", C.c_int64)]
+
+
+class KernelProf(C.Structure):
+    _fields_ = [("launches", C.c_int), ("jobs", C.c_int), ("ms", C.c_double), ("flops", C.c_double),
+                ("bytes", C.c_double)]
+
+
+class H2Error(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib().h2_strerror(code).decode() if _LIB is not None else str(code)
+        extra = _lib().h2_last_cuda_error().decode() if _LIB is not None else ""
+        super().__init__(f"{where}: {msg} ({code}) {extra}".strip())
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        lib = C.CDLL(LIB_PATH)
+        vp, i64, dp = C.c_void_p, C.c_int64, C.POINTER(C.c_double)
+        lib.h2_build.argtypes = [dp, i64, C.POINTER(BuildOpts), C.POINTER(vp)]
+        lib.h2_mul.argtypes = [vp, vp, C.c_double, C.POINTER(MulOpts), C.POINTER(vp)]
+        lib.h2_check.argtypes = [vp]
+        lib.h2_mul_profile.argtypes = [vp, vp, C.c_double, C.POINTER(MulOpts), C.POINTER(KernelProf), C.POINTER(vp)]
+        lib.h2_matvec.argtypes = [vp, vp, vp, C.c_int]
+        lib.h2_to_dense.argtypes = [vp, vp, C.c_int]
+        lib.h2_info.argtypes = [vp, C.POINTER(Stats)]
+        lib.h2_ranks.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        lib.h2_permutation.argtypes = [vp, C.POINTER(C.c_int64)]
+        lib.h2_free.argtypes = [vp]
+        lib.h2_free.restype = None
+        lib.h2_strerror.argtypes = [C.c_int]
+        lib.h2_strerror.restype = C.c_char_p
+        lib.h2_last_cuda_error.argtypes = []
+        lib.h2_last_cuda_error.restype = C.c_char_p
+        _LIB = lib
+    return _LIB
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise H2Error(rc, where)
+
+
+class H2Matrix:
+    """Owning wrapper of an h2_matrix handle."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h and self._h.value:
+            _lib().h2_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> Stats:
+        st = Stats()
+        _check(_lib().h2_info(self._h, C.byref(st)), "h2_info")
+        return st
+
+    def ranks(self):
+        st = self.info()
+        rr = (C.c_int * st.nclusters)()
+        rc = (C.c_int * st.nclusters)()
+        _check(_lib().h2_ranks(self._h, rr, rc), "h2_ranks")
+        return np.array(rr[:], dtype=np.int64), np.array(rc[:], dtype=np.int64)
+
+    def permutation(self):
+        st = self.info()
+        p = (C.c_int64 * st.n)()
+        _check(_lib().h2_permutation(self._h, p), "h2_permutation")
+        return np.array(p[:], dtype=np.int64)
+
+    def matvec(self, x):
+        """y = A x for a host vector (numpy) or a CUDA torch tensor."""
+        if hasattr(x, "is_cuda") and x.is_cuda:
+            import torch
+            y = torch.empty_like(x)
+            _check(_lib().h2_matvec(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), 1), "h2_matvec")
+            return y
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty_like(x)
+        _check(_lib().h2_matvec(self._h, x.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p), 0),
+               "h2_matvec")
+        return y
+
+    def to_dense(self):
+        st = self.info()
+        out = np.empty((st.n, st.n), dtype=np.float64, order="F")
+        _check(_lib().h2_to_dense(self._h, out.ctypes.data_as(C.c_void_p), 0), "h2_to_dense")
+        return np.ascontiguousarray(out)
+
+    def check(self):
+        _check(_lib().h2_check(self._h), "h2_check")
+
+
+def build(points, kernel, eta, leaf_size, order) -> H2Matrix:
+    """h2_build on host points (n, dim) with a KernelSpec (inputs.py)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    n, dim = pts.shape
+    o = BuildOpts()
+    o.eta, o.leaf_size, o.order, o.kernel, o.dim = float(eta), int(leaf_size), int(order), int(kernel.kind), int(dim)
+    for i, v in enumerate(kernel.kparam()):
+        o.kparam[i] = v
+    h = C.c_void_p()
+    _check(_lib().h2_build(pts.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(o), C.byref(h)), "h2_build")
+    return H2Matrix(h.value)
+
+
+def mul(A: H2Matrix, B: H2Matrix, eps: float, max_rank: int = 0, theta: float = 0.0, sync: bool = True,
+        stream=None) -> H2Matrix:
+    """C ~ A*B with block-relative error eps (h2_mul)."""
+    o = MulOpts()
+    o.theta, o.max_rank, o.precision, o.sync = float(theta), int(max_rank), 0, 1 if sync else 0
+    o.stream = stream
+    h = C.c_void_p()
+    _check(_lib().h2_mul(A.handle, B.handle, float(eps), C.byref(o), C.byref(h)), "h2_mul")
+    return H2Matrix(h.value)
+
+
+def mul_profile(A: H2Matrix, B: H2Matrix, eps: float, prof, max_rank: int = 0, stream=None) -> H2Matrix:
+    """h2_mul_profile: the product with per-kernel-kind device times and work in `prof`
+    (an array of 7 KernelProf)."""
+    o = MulOpts()
+    o.theta, o.max_rank, o.precision, o.sync = 0.0, int(max_rank), 0, 1
+    o.stream = stream
+    h = C.c_void_p()
+    _check(_lib().h2_mul_profile(A.handle, B.handle, float(eps), C.byref(o), prof, C.byref(h)), "h2_mul_profile")
+    return H2Matrix(h.value)
+
+
+def exported_symbols():
+    """Entry points declared in include/h2.h (parsed from the header)."""
+    import re
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(h2_[a-z_]+)\s*\(", text)))
