@@ -177,8 +177,12 @@ def main():
     w = I.grid_2d(GRID, EPS)
     A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
     B = h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the legacy default stream has handle 0, which the
+    # library would read as "use the library stream"
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
+    assert sptr != 0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # warm-up (plan build, graph capture, pool growth)
