@@ -154,6 +154,23 @@ int h2_ranks(const h2_matrix* A, int* row_ranks, int* col_ranks);
 /* Cluster-order permutation: perm[i] = original index of the i-th point. */
 int h2_permutation(const h2_matrix* A, int64_t* perm);
 
+/* y = A x without any allocation, for callers that cannot call cudaMalloc
+ * (work enqueued inside a CUDA stream capture, where allocation is not a
+ * capturable operation; latency-critical loops that must stay out of the
+ * allocator; devices whose memory is partitioned up front).  The paper has no
+ * counterpart: this is a convenience of the library.
+ *   x, y    DEVICE vectors of length n in the library's CLUSTER ordering
+ *           (h2_permutation maps it to the caller's ordering); y is overwritten
+ *   stream  cudaStream_t to enqueue on (NULL: legacy default stream); the call
+ *           returns without waiting for the GPU
+ * Scratch: one static device array of 2^20 doubles (8 MiB) in every process and
+ * on every GPU that loads the library, held until exit.  A call needs
+ * 2 * nclusters * kpad doubles of it and returns H2_ENOMEM beyond that.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race; serialise them. */
+int h2_matvec_noalloc(const h2_matrix* A, const double* x, double* y, void* stream);
+
 void h2_free(h2_matrix* A);
 
 const char* h2_strerror(int code);
