@@ -29,14 +29,14 @@ METRIC = "H²×H² products/s at block-rel eps=1e-6, chosen vs plain FP64 form; 
 UNIT = "products/s"
 GRID = 128
 EPS = 1e-6
-KIND_NAMES = ["k_gemm", "k_copy", "k_qr", "k_qapply", "k_svd", "k_scan", "k_finalize"]
+KIND_NAMES = ["k_gemm", "k_copy", "k_qr", "k_qapply", "k_svd", "k_scan", "k_finalize", "k_norm"]
 
 
-def workload_config():
+def workload_config(grid=GRID):
     return {
-        "workload": f"grid2d_n{GRID * GRID}: C=A*B, A=-log|x-y|/(2pi) diag 1, B=exp(-|x-y|^2/0.1), "
+        "workload": f"grid2d_n{grid * grid}: C=A*B, A=-log|x-y|/(2pi) diag 1, B=exp(-|x-y|^2/0.1), "
                     f"leaf 64, eta 2, Chebyshev order 4 (k=16), eps={EPS:g}",
-        "n": GRID * GRID, "k": 16, "leaf_size": 64, "eta": 2.0, "eps": EPS, "form": "plain FP64",
+        "n": grid * grid, "k": 16, "leaf_size": 64, "eta": 2.0, "eps": EPS, "form": "plain FP64",
         "l2": "flushed between timed steps (256 MiB write)",
     }
 
@@ -154,6 +154,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=GRID,
+                    help="grid side (default 128 = the benchmark workload; smaller for profiler captures)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -174,7 +176,8 @@ def main():
     from paper_2403_01566_gb300 import h2
     from paper_2403_01566_gb300 import inputs as I
 
-    w = I.grid_2d(GRID, EPS)
+    grid = args.grid
+    w = I.grid_2d(grid, EPS)
     A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
     B = h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order)
     # a dedicated stream: the legacy default stream has handle 0, which the
@@ -246,10 +249,10 @@ def main():
     assert np.isfinite(y).all()
 
     # roofline of the dominant kernel: one profiled product (stages one by one)
-    prof = (h2.KernelProf * 7)()
+    prof = (h2.KernelProf * len(KIND_NAMES))()
     Cp = h2.mul_profile(A, B, EPS, prof, stream=sptr)
     Cp.free()
-    kinds = [(KIND_NAMES[i], prof[i]) for i in range(7)]
+    kinds = [(KIND_NAMES[i], prof[i]) for i in range(len(KIND_NAMES))]
     prof_total = sum(p.ms for _, p in kinds)
     dom_name, dom = max(kinds, key=lambda kv: kv[1].ms)
     peak = fp64_peak()
@@ -263,7 +266,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        ts = oracle_subprocess(GRID, EPS, 1)
+        ts = oracle_subprocess(grid, EPS, 1)
         cpu = {"value": 1.0 / ts[0], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one full product of the workload on one host thread (numpy FP64 oracle, "
                          "input build excluded)"}
@@ -276,7 +279,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(), parallelism=f"replicas x{world}"),
+            "config": dict(workload_config(grid), parallelism=f"replicas x{world}"),
             "p50_ms": p50, "p99_ms": p99, "wall_s": t_wall,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * w.points.nbytes + x.nbytes), "d2h_bytes_per_step": int(x.nbytes),

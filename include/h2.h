@@ -117,12 +117,13 @@ int h2_mul(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts
  * summed device time (CUDA events around every stage on the product's stream)
  * and the algorithmic work of one product computed like h2_mul.  Kinds:
  * 0 batched GEMM, 1 copy, 2 Householder QR, 3 Q application, 4 Jacobi SVD,
- * 5 rank prefix sums, 6 finalize.  flops count the FP64 operations of the
- * algorithm with the ranks the device decided (Householder QR 2mn^2 - 2n^3/3,
- * one-sided Jacobi 6 m n (n-1) per executed sweep); bytes are the algorithmic
+ * 5 rank prefix sums, 6 finalize, 7 block norms.  flops count the FP64 operations of the
+ * algorithm with the ranks the device decided (Householder QR 2mn^2 - 2n^3/3;
+ * one-sided Jacobi m n (n-1) + 2mn per executed sweep plus 6m per applied
+ * rotation); bytes are the algorithmic
  * reads and writes of each job.  The stages run one by one (no graph).
  * `out` must hold H2_PROFILE_KINDS entries.  The product is returned in *C. */
-#define H2_PROFILE_KINDS 7
+#define H2_PROFILE_KINDS 8
 typedef struct {
   int launches;
   int jobs;

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -107,7 +108,7 @@ static int upload_plan(PlanRT& rt, const std::vector<int>& rank_src) {
   Plan& P = *rt.plan;
   std::vector<char> blob;
   const size_t o_go = put(blob, P.gout), o_gt = put(blob, P.gterm), o_cp = put(blob, P.copy), o_qr = put(blob, P.qr),
-               o_qa = put(blob, P.qap), o_sv = put(blob, P.svd), o_sc = put(blob, P.scan),
+               o_qa = put(blob, P.qap), o_sv = put(blob, P.svd), o_sc = put(blob, P.scan), o_nm = put(blob, P.norm),
                o_si = put(blob, P.slot_init), o_ix = put(blob, P.idx), o_k = put(blob, P.konst),
                o_rs = put(blob, rank_src);
   CK(cudaMalloc(&rt.d_blob, std::max<size_t>(blob.size(), 256)));
@@ -120,6 +121,7 @@ static int upload_plan(PlanRT& rt, const std::vector<int>& rank_src) {
   rt.dj.qapply = (const QApplyJob*)(b + o_qa);
   rt.dj.svd = (const SvdJob*)(b + o_sv);
   rt.dj.scan = (const ScanJob*)(b + o_sc);
+  rt.dj.norm = (const NormJob*)(b + o_nm);
   rt.d_slot_init = (int*)(b + o_si);
   rt.d_idx = (int*)(b + o_ix);
   rt.d_konst = (double*)(b + o_k);
@@ -217,8 +219,8 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
                              cudaStream_t s, h2_kernel_prof* prof) {
   Plan& P = *rt.plan;
   int* d_sweeps = nullptr;
-  CK(cudaMalloc(&d_sweeps, sizeof(int) * std::max<size_t>(P.svd.size(), 1)));
-  CK(cudaMemset(d_sweeps, 0, sizeof(int) * std::max<size_t>(P.svd.size(), 1)));
+  CK(cudaMalloc(&d_sweeps, 2 * sizeof(int) * std::max<size_t>(P.svd.size(), 1)));
+  CK(cudaMemset(d_sweeps, 0, 2 * sizeof(int) * std::max<size_t>(P.svd.size(), 1)));
   ExecCtx ctx{};
   ctx.base[AR_WS] = rt.d_ws;
   ctx.base[AR_X] = bx;
@@ -255,7 +257,7 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
   CK(cudaGetLastError());
   CK(cudaEventRecord(rt.last, s));
   CK(cudaStreamSynchronize(s));
-  std::vector<int> slot(P.slot_init.size()), sweeps(P.svd.size());
+  std::vector<int> slot(P.slot_init.size()), sweeps(2 * P.svd.size());
   if (!slot.empty()) CK(cudaMemcpy(slot.data(), rt.d_slot, slot.size() * 4, cudaMemcpyDeviceToHost));
   if (!sweeps.empty()) CK(cudaMemcpy(sweeps.data(), d_sweeps, sweeps.size() * 4, cudaMemcpyDeviceToHost));
   cudaFree(d_sweeps);
@@ -263,19 +265,23 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
     int v = d.c;
     if (d.s1 >= 0) v += slot[d.s1];
     if (d.s2 >= 0) v += slot[d.s2];
+    if (d.mc >= 0) v = std::min(v, d.mc + (d.ms >= 0 ? slot[d.ms] : 0));
     return (double)v;
   };
   for (int k = 0; k < H2_PROFILE_KINDS; ++k) prof[k] = h2_kernel_prof{0, 0, 0.0, 0.0, 0.0};
+  // H2_PROFILE_STAGES=1 prints one line per stage to stderr (diagnostics)
+  const bool verbose = std::getenv("H2_PROFILE_STAGES") != nullptr;
   for (size_t i = 0; i <= ns; ++i) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
-    const int kind = i < ns ? P.stages[i].kind : 6;
+    const int kind = i < ns ? (P.stages[i].kind == ST_NORM ? 7 : P.stages[i].kind) : 6;
     h2_kernel_prof& pr = prof[kind];
     pr.launches += 1;
     pr.ms += ms;
     if (i == ns) continue;
     const Stage& st = P.stages[i];
     pr.jobs += st.count;
+    double st_fl = 0.0;
     for (int j = 0; j < st.count; ++j) {
       double fl = 0, by = 0;
       const int64_t J = st.first + j;
@@ -322,10 +328,19 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
           by += 8 * (r * q + 2 * r * nc);
           break;
         }
+        case ST_NORM: {
+          // N^T N (symmetric half), tridiagonalisation (4/3 n^3)
+          const double n = dv(P.norm[J].n);
+          fl += n * n * (n + 1) + 4.0 * n * n * n / 3.0;
+          by += 8 * n * n;
+          break;
+        }
         case ST_SVD: {
           const SvdJob& S = P.svd[J];
           const double r = dv(S.rows), c = dv(S.cols);
-          fl += 6 * r * c * (c - 1) * sweeps[J] + 2 * r * c;
+          // per sweep: one dot product per pair and the column norms; 6 flops per
+          // row for each applied rotation
+          fl += (r * c * (c - 1) + 2 * r * c) * sweeps[2 * J] + 6 * r * sweeps[2 * J + 1] + 2 * r * c;
           by += 16 * r * c;
           break;
         }
@@ -334,7 +349,11 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
       }
       pr.flops += fl;
       pr.bytes += by;
+      st_fl += fl;
     }
+    if (verbose)
+      std::fprintf(stderr, "stage %4zu kind %d tag %2d jobs %7d smem %6d ms %9.4f gflop %9.4f tflops %6.3f\n", i,
+                   st.kind, st.tag, st.count, st.smem, ms, st_fl / 1e9, ms > 0 ? st_fl / ms / 1e9 : 0.0);
   }
   for (auto& e : ev) cudaEventDestroy(e);
   return H2_OK;

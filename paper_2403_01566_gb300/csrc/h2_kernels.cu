@@ -20,6 +20,7 @@ __device__ __forceinline__ int dimv(const Dim& d, const int* slot) {
   int v = d.c;
   if (d.s1 >= 0) v += slot[d.s1];
   if (d.s2 >= 0) v += slot[d.s2];
+  if (d.mc >= 0) v = min(v, d.mc + (d.ms >= 0 ? slot[d.ms] : 0));
   return v;
 }
 
@@ -36,12 +37,47 @@ __device__ __forceinline__ void set_err(const ExecCtx& x, int code) {
 }
 
 // ------------------------------------------------------------------ GEMM ----
-// Output tile up to GT x GT, 256 threads, each thread 4x4 outputs.
+// Output tile up to GT x GT; the 256 threads are mapped onto the actual output
+// elements (element e = tid + 256 q), so small outputs (16 x 16 coupling and
+// transfer products) waste no FP64 FMA.  Operand chunks of GK columns are
+// staged in shared memory; each output is a dot product over the chunk.
 constexpr int GT = 64;
 constexpr int GK = 32;
+constexpr int GQ = (GT * GT) / 256;  // outputs per thread at most
 
 __device__ __forceinline__ double ld_op(const double* p, int ld, int t, int i, int j) {
   return t ? p[(int64_t)j * ld + i] : p[(int64_t)i * ld + j];
+}
+
+// acc[q] += op(A)(m x k) op(B)(k x n) for the outputs of this thread
+__device__ __forceinline__ void gemm_accumulate(double (&acc)[GQ], int nq, int m, int n, int k, const double* A,
+                                                int lda, int ta, const double* B, int ldb, int tb, double* As,
+                                                double* Bs) {
+  for (int kk = 0; kk < k; kk += GK) {
+    const int kc = min(GK, k - kk);
+    for (int e = threadIdx.x; e < m * kc; e += 256) {
+      const int r = e / kc, l = e % kc;
+      As[r * (GK + 1) + l] = ld_op(A, lda, ta, r, kk + l);
+    }
+    for (int e = threadIdx.x; e < kc * n; e += 256) {
+      const int l = e / n, c = e % n;
+      Bs[l * (GT + 1) + c] = ld_op(B, ldb, tb, kk + l, c);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < GQ; ++q) {
+      if (q < nq) {
+        const int e = threadIdx.x + 256 * q;
+        if (e < m * n) {
+          const int r = e / n, c = e % n;
+          double a = acc[q];
+          for (int l = 0; l < kc; ++l) a = fma(As[r * (GK + 1) + l], Bs[l * (GT + 1) + c], a);
+          acc[q] = a;
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs,
@@ -59,12 +95,10 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     if (threadIdx.x == 0) set_err(x, -9);
     return;
   }
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  const int nq = (m * n + 255) / 256;
+  double acc[GQ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int q = 0; q < GQ; ++q) acc[q] = 0.0;
 
   for (int ti = O.t0; ti < O.t1; ++ti) {
     const GemmTerm& T = terms[ti];
@@ -75,94 +109,75 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     const double* C = ptrv(T.c, x);
     if (B == nullptr) {  // plain add of op(A) (m x n)
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          int r = ty + 16 * i, c = tx + 16 * j;
-          if (r < m && c < n) acc[i][j] += alpha * ld_op(A, T.lda, T.ta, r, c);
-        }
+      for (int q = 0; q < GQ; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        if (q < nq && e < m * n) acc[q] += alpha * ld_op(A, T.lda, T.ta, e / n, e % n);
+      }
       continue;
     }
     const int k1 = dimv(T.k1, x.slot);
-    const int nn = C ? dimv(T.k2, x.slot) : n;  // columns of op(A)op(B)
-    if (C && nn > GT) {
-      if (threadIdx.x == 0) set_err(x, -9);
-      return;
-    }
-    double tacc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) tacc[i][j] = 0.0;
-    for (int kk = 0; kk < k1; kk += GK) {
-      const int kc = min(GK, k1 - kk);
-      for (int e = threadIdx.x; e < GT * GK; e += 256) {
-        int r = e / GK, l = e % GK;
-        As[r * (GK + 1) + l] = (r < m && l < kc) ? ld_op(A, T.lda, T.ta, r, kk + l) : 0.0;
-      }
-      for (int e = threadIdx.x; e < GK * GT; e += 256) {
-        int l = e / GT, c = e % GT;
-        Bs[l * (GT + 1) + c] = (l < kc && c < nn) ? ld_op(B, T.ldb, T.tb, kk + l, c) : 0.0;
-      }
-      __syncthreads();
-      for (int l = 0; l < kc; ++l) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[(ty + 16 * i) * (GK + 1) + l];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[l * (GT + 1) + tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) tacc[i][j] = fma(av[i], bv[j], tacc[i][j]);
-      }
-      __syncthreads();
-    }
     if (C == nullptr) {
+      double tacc[GQ];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int q = 0; q < GQ; ++q) tacc[q] = 0.0;
+      gemm_accumulate(tacc, nq, m, n, k1, A, T.lda, T.ta, B, T.ldb, T.tb, As, Bs);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += alpha * tacc[i][j];
+      for (int q = 0; q < GQ; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
       continue;
     }
     // three-factor term: Ts = op(A)op(B) (m x nn), then acc += alpha * Ts op(C)
+    const int nn = dimv(T.k2, x.slot);
+    if (nn > GT) {
+      if (threadIdx.x == 0) set_err(x, -9);
+      return;
+    }
+    const int nq2 = (m * nn + 255) / 256;
+    double tacc[GQ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int q = 0; q < GQ; ++q) tacc[q] = 0.0;
+    gemm_accumulate(tacc, nq2, m, nn, k1, A, T.lda, T.ta, B, T.ldb, T.tb, As, Bs);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) Ts[(ty + 16 * i) * (GT + 1) + tx + 16 * j] = tacc[i][j];
+    for (int q = 0; q < GQ; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if (q < nq2 && e < m * nn) Ts[(e / nn) * (GT + 1) + e % nn] = tacc[q];
+    }
     __syncthreads();
+#pragma unroll
+    for (int q = 0; q < GQ; ++q) tacc[q] = 0.0;
+    // Ts (m x nn) times op(C) (nn x n); Ts plays the role of A (already in smem)
     for (int kk = 0; kk < nn; kk += GK) {
       const int kc = min(GK, nn - kk);
-      for (int e = threadIdx.x; e < GK * GT; e += 256) {
-        int l = e / GT, c = e % GT;
-        Bs[l * (GT + 1) + c] = (l < kc && c < n) ? ld_op(C, T.ldc, T.tc, kk + l, c) : 0.0;
+      for (int e = threadIdx.x; e < kc * n; e += 256) {
+        const int l = e / n, c = e % n;
+        Bs[l * (GT + 1) + c] = ld_op(C, T.ldc, T.tc, kk + l, c);
       }
       __syncthreads();
-      for (int l = 0; l < kc; ++l) {
-        double av[4], bv[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = Ts[(ty + 16 * i) * (GT + 1) + kk + l];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[l * (GT + 1) + tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(alpha * av[i], bv[j], acc[i][j]);
+      for (int q = 0; q < GQ; ++q) {
+        if (q < nq) {
+          const int e = threadIdx.x + 256 * q;
+          if (e < m * n) {
+            const int r = e / n, c = e % n;
+            double a = tacc[q];
+            for (int l = 0; l < kc; ++l) a = fma(Ts[r * (GT + 1) + kk + l], Bs[l * (GT + 1) + c], a);
+            tacc[q] = a;
+          }
+        }
       }
       __syncthreads();
     }
+#pragma unroll
+    for (int q = 0; q < GQ; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
   }
   double* out = ptrv(O.o, x);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int r = ty + 16 * i, c = tx + 16 * j;
-      if (r < m && c < n) {
-        double* p = out + (int64_t)r * O.ldo + c;
-        *p = O.beta ? (*p + acc[i][j]) : acc[i][j];
-      }
+  for (int q = 0; q < GQ; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    if (q < nq && e < m * n) {
+      double* p = out + (int64_t)(e / n) * O.ldo + e % n;
+      *p = O.beta ? (*p + acc[q]) : acc[q];
     }
+  }
 }
 
 // ------------------------------------------------------------------ copy ----
@@ -208,61 +223,95 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-__global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, const QrJob* __restrict__ jobs) {
-  const ExecCtx& x = *px;
-  __shared__ double red[32];
-  __shared__ double sh_tau;
-  const QrJob& J = jobs[blockIdx.x];
-  const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
-  double* a = ptrv(J.a, x);
-  double* tau = ptrv(J.tau, x);
-  const int lda = J.lda;
+// Householder on a column-major matrix a (rows x cols, leading dimension lda),
+// one warp per trailing column; `a` is global or shared memory.
+__device__ void householder_cols(double* a, int lda, int rows, int cols, double* tau, double* red, double* sh) {
   const int q = min(rows, cols);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = 0; j < q; ++j) {
     double* col = a + (int64_t)j * lda;
     double s2 = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) s2 += col[i] * col[i];
+    for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) s2 = fma(col[i], col[i], s2);
     s2 = block_sum(s2, red);
     if (threadIdx.x == 0) {
       const double alpha = col[j];
-      double t = 0.0;
+      double t = 0.0, sc = 0.0;
       if (s2 > 0.0) {
         const double beta = -copysign(sqrt(alpha * alpha + s2), alpha);
         t = (beta - alpha) / beta;
-        red[1] = 1.0 / (alpha - beta);
+        sc = 1.0 / (alpha - beta);
         col[j] = beta;
-      } else {
-        red[1] = 0.0;
       }
-      sh_tau = t;
+      sh[0] = t;
+      sh[1] = sc;
       if (tau) tau[j] = t;
     }
     __syncthreads();
-    const double t = sh_tau, sc = red[1];
-    if (t != 0.0)
-      for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) col[i] *= sc;
-    __syncthreads();
+    const double t = sh[0], sc = sh[1];
     if (t != 0.0) {
+      for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) col[i] *= sc;
+      __syncthreads();
       for (int c = j + 1 + warp; c < cols; c += nw) {
         double* cc = a + (int64_t)c * lda;
         double p = 0.0;
-        for (int i = j + 1 + lane; i < rows; i += 32) p += col[i] * cc[i];
+        for (int i = j + 1 + lane; i < rows; i += 32) p = fma(col[i], cc[i], p);
         p = warp_sum(p);
         const double w = t * (cc[j] + p);
         if (lane == 0) cc[j] -= w;
-        for (int i = j + 1 + lane; i < rows; i += 32) cc[i] -= w * col[i];
+        for (int i = j + 1 + lane; i < rows; i += 32) cc[i] = fma(-w, col[i], cc[i]);
       }
     }
     __syncthreads();
   }
+}
+
+constexpr int QR_SMEM_DOUBLES = 6144;  // 48 KB: in-shared-memory QR up to this size
+
+__global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, const QrJob* __restrict__ jobs,
+                                            int smem_doubles) {
+  const ExecCtx& x = *px;
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ double sh[2];
+  const QrJob& J = jobs[blockIdx.x];
+  const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
+  double* a = ptrv(J.a, x);
+  double* tau = ptrv(J.tau, x);
   double* r = ptrv(J.r, x);
-  if (r) {
+  const int lda = J.lda;
+  const int q = min(rows, cols);
+  if (rows <= 0 || cols <= 0) {
+    if (r)
+      for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) r[(int64_t)(e / cols) * J.ldr + e % cols] = 0.0;
+    return;
+  }
+  if ((int64_t)rows * cols <= smem_doubles) {
+    // whole matrix in shared memory
+    for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
+      const int c = (int)(e / rows), i = (int)(e % rows);
+      sm[e] = a[(int64_t)c * lda + i];
+    }
+    __syncthreads();
+    householder_cols(sm, rows, rows, cols, tau, red, sh);
+    if (J.keep)
+      for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
+        const int c = (int)(e / rows), i = (int)(e % rows);
+        a[(int64_t)c * lda + i] = sm[e];
+      }
+    if (r)
+      for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
+        const int i = e / cols, c = e % cols;
+        r[(int64_t)i * J.ldr + c] = (c >= i && i < q) ? sm[(int64_t)c * rows + i] : 0.0;
+      }
+    return;
+  }
+  // general case: in place in global memory
+  householder_cols(a, lda, rows, cols, tau, red, sh);
+  if (r)
     for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
-      int i = e / cols, c = e % cols;
+      const int i = e / cols, c = e % cols;
       r[(int64_t)i * J.ldr + c] = (c >= i && i < q) ? a[(int64_t)c * lda + i] : 0.0;
     }
-  }
 }
 
 __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, const QApplyJob* __restrict__ jobs) {
@@ -298,6 +347,14 @@ __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, 
 }
 
 // ------------------------------------------------------------------- SVD ----
+// One-sided (Hestenes) Jacobi: rotate pairs of columns of M until all pairs are
+// orthogonal to relative precision; the column norms are the singular values
+// and the normalised columns the left singular vectors.  Pairs follow the
+// round-robin (circle) ordering so that cols/2 disjoint pairs rotate at once,
+// each by a team of lanes.  Squared column norms are kept in shared memory,
+// updated after each rotation (alpha' = alpha - t*gamma, beta' = beta + t*gamma)
+// and recomputed exactly at the start of every sweep, so a pair costs one dot
+// product plus the rotation.
 constexpr int SVD_MAXSWEEP = 60;
 
 __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, const SvdJob* __restrict__ jobs,
@@ -305,8 +362,11 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
   const ExecCtx& x = *px;
   extern __shared__ double sm[];
   __shared__ int rotated;
+  __shared__ int nrot;
+  __shared__ double nrm2[SVD_MAXDIM];
   __shared__ double snorm[SVD_MAXDIM];
   __shared__ int spos[SVD_MAXDIM];
+  __shared__ double s_fro;
   const SvdJob& J = jobs[blockIdx.x];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
   int* rank_out = (J.rank_slot >= 0) ? x.slot + J.rank_slot : nullptr;
@@ -334,24 +394,28 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
     int r = e / cols, c = e % cols;
     M[c * ldm + r] = J.trans ? S[(int64_t)c * J.lds + r] : S[(int64_t)r * J.lds + c];
   }
+  if (threadIdx.x == 0) nrot = 0;
   __syncthreads();
-  // Frobenius norm (invariant under the rotations); columns whose norm falls
-  // below 2^-50 ||M||_F are rounding noise: they are not rotated and count as
-  // sigma = 0 (otherwise noise re-created by neighbouring rotations keeps the
-  // sweeps from converging and yields non-orthogonal vectors).
-  __shared__ double s_fro;
-  {
-    double p = 0.0;
-    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-      const int r = e / cols, c = e % cols;
-      const double v = M[c * ldm + r];
-      p = fma(v, v, p);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  // exact squared column norms (one warp per column)
+  auto col_norms = [&]() {
+    for (int c = warp; c < cols; c += nwarp) {
+      double p = 0.0;
+      for (int r = lane; r < rows; r += 32) p = fma(M[c * ldm + r], M[c * ldm + r], p);
+      p = warp_sum(p);
+      if (lane == 0) nrm2[c] = p;
     }
-    p = block_sum(p, snorm);
-    if (threadIdx.x == 0) s_fro = p;
     __syncthreads();
+  };
+  col_norms();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int c = 0; c < cols; ++c) f += nrm2[c];
+    s_fro = f;
   }
-  const double tiny2 = s_fro * 7.888609052210118e-31;  // (2^-50)^2 ||M||_F^2
+  __syncthreads();
+  // columns below 2^-50 ||M||_F are rounding noise: never rotated, sigma = 0
+  const double tiny2 = s_fro * 7.888609052210118e-31;
   const int ce = cols + (cols & 1);
   const int npairs = ce / 2;
   int ts = 32;
@@ -373,58 +437,73 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
           j = (rnd - team + ce - 1) % (ce - 1);
         }
         if (i > j) {
-          int t = i;
+          const int t = i;
           i = j;
           j = t;
         }
       }
       const bool valid = team < npairs && j < cols;
-      double al = 0.0, be = 0.0, ga = 0.0;
+      double ga = 0.0;
       if (valid) {
         const double* mi = M + i * ldm;
         const double* mj = M + j * ldm;
-        for (int r = tl; r < rows; r += ts) {
-          const double u = mi[r], v = mj[r];
-          al = fma(u, u, al);
-          be = fma(v, v, be);
-          ga = fma(u, v, ga);
+        double g2 = 0.0;
+        int r = tl;
+        for (; r + ts < rows; r += 2 * ts) {
+          ga = fma(mi[r], mj[r], ga);
+          g2 = fma(mi[r + ts], mj[r + ts], g2);
+        }
+        if (r < rows) ga = fma(mi[r], mj[r], ga);
+        ga += g2;
+      }
+      for (int o = ts >> 1; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      // rotation parameters on the team leader only (FP64 sqrt/div are long
+      // instruction sequences), broadcast to the team
+      double c = 1.0, sn = 0.0;
+      int rot = 0;
+      if (valid && tl == 0) {
+        const double al = nrm2[i], be = nrm2[j];
+        // |ga| > tol * sqrt(al * be), in squared form
+        if (ga != 0.0 && al > tiny2 && be > tiny2 && ga * ga > (tol * tol) * al * be) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          c = rsqrt(1.0 + t * t);
+          sn = c * t;
+          rot = 1;
+          nrm2[i] = fmax(al - t * ga, 0.0);
+          nrm2[j] = be + t * ga;
+          rotated = 1;
+          atomicAdd(&nrot, 1);
         }
       }
-      for (int o = ts >> 1; o > 0; o >>= 1) {
-        al += __shfl_xor_sync(0xffffffffu, al, o);
-        be += __shfl_xor_sync(0xffffffffu, be, o);
-        ga += __shfl_xor_sync(0xffffffffu, ga, o);
-      }
-      if (valid && ga != 0.0 && al > tiny2 && be > tiny2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t);
-        const double s = c * t;
+      const int leader = (threadIdx.x & 31) & ~(ts - 1);
+      rot = __shfl_sync(0xffffffffu, rot, leader);
+      c = __shfl_sync(0xffffffffu, c, leader);
+      sn = __shfl_sync(0xffffffffu, sn, leader);
+      if (valid && rot) {
         double* mi = M + i * ldm;
         double* mj = M + j * ldm;
         for (int r = tl; r < rows; r += ts) {
           const double u = mi[r], v = mj[r];
-          mi[r] = c * u - s * v;
-          mj[r] = s * u + c * v;
+          mi[r] = fma(c, u, -sn * v);
+          mj[r] = fma(sn, u, c * v);
         }
-        if (tl == 0) rotated = 1;
       }
       __syncthreads();
     }
     if (!rotated) break;
-    __syncthreads();
+    col_norms();
   }
   if (threadIdx.x == 0) {
     if (sweep >= SVD_MAXSWEEP) set_err(x, -5);
-    if (x.svd_sweeps) x.svd_sweeps[first + blockIdx.x] = sweep + 1;
+    if (x.svd_sweeps) {
+      x.svd_sweeps[2 * (first + blockIdx.x)] = sweep + 1;
+      x.svd_sweeps[2 * (first + blockIdx.x) + 1] = nrot;
+    }
   }
-  // column norms = singular values
-  for (int c = threadIdx.x >> 5; c < cols; c += blockDim.x >> 5) {
-    double s = 0.0;
-    for (int r = threadIdx.x & 31; r < rows; r += 32) s = fma(M[c * ldm + r], M[c * ldm + r], s);
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) snorm[c] = (s > tiny2) ? sqrt(s) : 0.0;
-  }
+  // singular values = column norms (exact), sorted descending
+  col_norms();
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) snorm[c] = nrm2[c] > tiny2 ? sqrt(nrm2[c]) : 0.0;
   __syncthreads();
   for (int c = threadIdx.x; c < cols; c += blockDim.x) {
     const double v = snorm[c];
@@ -472,6 +551,121 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
   }
 }
 
+// ------------------------------------------------------------------ norm ----
+// ||N||_2^2 = lambda_max(G), G = N^T N: Householder tridiagonalisation of G in
+// shared memory (symmetric rank-2 updates), then bisection with Sturm counts on
+// the tridiagonal matrix for its largest eigenvalue.
+__global__ void __launch_bounds__(256) k_norm(const ExecCtx* __restrict__ px, const NormJob* __restrict__ jobs) {
+  const ExecCtx& x = *px;
+  constexpr int NM = GT;  // n <= 64
+  extern __shared__ double sm[];
+  double* Ns = sm;                  // NM x (NM+1)
+  double* G = sm + NM * (NM + 1);   // NM x (NM+1)
+  __shared__ double v[NM], p[NM], w[NM], d[NM], e[NM];
+  __shared__ double red[32];
+  __shared__ double sh[4];
+  const NormJob& J = jobs[blockIdx.x];
+  const int n = dimv(J.n, x.slot);
+  if (n <= 0 || n > NM) {
+    if (threadIdx.x == 0) {
+      if (n > NM) set_err(x, -9);
+      x.nrm[J.norm_idx] = 0.0;
+      x.scal[J.norm_idx] = 0.0;
+    }
+    return;
+  }
+  const double* S = ptrv(J.src, x);
+  const int ld = NM + 1;
+  for (int e2 = threadIdx.x; e2 < n * n; e2 += blockDim.x) Ns[(e2 / n) * ld + e2 % n] = S[(int64_t)(e2 / n) * J.lds + e2 % n];
+  __syncthreads();
+  // G = N^T N (symmetric)
+  for (int e2 = threadIdx.x; e2 < n * n; e2 += blockDim.x) {
+    const int i = e2 / n, j = e2 % n;
+    if (j < i) continue;
+    double a = 0.0;
+    for (int l = 0; l < n; ++l) a = fma(Ns[l * ld + i], Ns[l * ld + j], a);
+    G[i * ld + j] = a;
+    G[j * ld + i] = a;
+  }
+  __syncthreads();
+  // tridiagonalisation: for column k, reflect rows/cols k+1..n-1
+  for (int k = 0; k + 2 < n; ++k) {
+    double s2 = 0.0;
+    for (int i = k + 2 + threadIdx.x; i < n; i += blockDim.x) s2 = fma(G[i * ld + k], G[i * ld + k], s2);
+    s2 = block_sum(s2, red);
+    if (threadIdx.x == 0) {
+      const double alpha = G[(k + 1) * ld + k];
+      double tau = 0.0, sc = 0.0, beta = alpha;
+      if (s2 > 0.0) {
+        beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+        tau = (beta - alpha) / beta;
+        sc = 1.0 / (alpha - beta);
+      }
+      sh[0] = tau;
+      sh[1] = sc;
+      e[k] = beta;
+      d[k] = G[k * ld + k];
+    }
+    __syncthreads();
+    const double tau = sh[0], sc = sh[1];
+    if (tau == 0.0) continue;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) v[i] = (i == k + 1) ? 1.0 : G[i * ld + k] * sc;
+    __syncthreads();
+    // p = tau * A v on the trailing block A = G[k+1.., k+1..]
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      double a = 0.0;
+      for (int j = k + 1; j < n; ++j) a = fma(G[i * ld + j], v[j], a);
+      p[i] = tau * a;
+    }
+    __syncthreads();
+    double pv = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) pv = fma(p[i], v[i], pv);
+    pv = block_sum(pv, red);
+    const double K = 0.5 * tau * pv;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) w[i] = p[i] - K * v[i];
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int e2 = threadIdx.x; e2 < m * m; e2 += blockDim.x) {
+      const int i = k + 1 + e2 / m, j = k + 1 + e2 % m;
+      G[i * ld + j] -= v[i] * w[j] + w[i] * v[j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (n >= 2) {
+      d[n - 2] = G[(n - 2) * ld + (n - 2)];
+      e[n - 2] = G[(n - 1) * ld + (n - 2)];
+    }
+    d[n - 1] = G[(n - 1) * ld + (n - 1)];
+    // largest eigenvalue of the tridiagonal (d, e) by bisection
+    double lo = d[0], hi = d[0];
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+      lo = fmin(lo, d[i] - r);
+      hi = fmax(hi, d[i] + r);
+    }
+    const double scale = fmax(fabs(lo), fabs(hi));
+    lo = fmax(lo, 0.0);  // G is positive semi-definite
+    for (int it = 0; it < 200 && hi - lo > 2.0e-16 * scale; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      // Sturm count: number of eigenvalues below mid
+      int cnt = 0;
+      double q = d[0] - mid;
+      cnt += q < 0.0;
+      for (int i = 1; i < n; ++i) {
+        if (q == 0.0) q = 1e-300;
+        q = d[i] - mid - e[i - 1] * e[i - 1] / q;
+        cnt += q < 0.0;
+      }
+      if (cnt == n) hi = mid;
+      else lo = mid;
+    }
+    const double s0 = sqrt(fmax(hi, 0.0));
+    x.nrm[J.norm_idx] = s0;
+    x.scal[J.norm_idx] = s0 > 0.0 ? 1.0 / s0 : 0.0;
+  }
+}
+
 // ------------------------------------------------------------------ scan ----
 __global__ void k_scan(const ExecCtx* __restrict__ px, const ScanJob* __restrict__ jobs, int count) {
   const ExecCtx& x = *px;
@@ -497,6 +691,7 @@ __global__ void k_finalize(const ExecCtx* __restrict__ px) {
 }
 
 // ------------------------------------------------------------- launchers ----
+size_t norm_smem_bytes() { return sizeof(double) * 2 * GT * (GT + 1); }
 size_t gemm_smem_bytes() { return sizeof(double) * (GT * (GK + 1) + GK * (GT + 1) + GT * (GT + 1)); }
 size_t svd_smem_bytes(int rows, int cols) { return sizeof(double) * (size_t)(rows + 1) * cols; }
 
@@ -505,6 +700,10 @@ static bool g_attr_done = false;
 cudaError_t kernels_init() {
   if (g_attr_done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * QR_SMEM_DOUBLES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)svd_smem_bytes(SVD_MAXDIM, SVD_MAXDIM));
@@ -527,13 +726,16 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t
       k_copy<<<st.count, 256, 0, s>>>(x, j.copy + st.first);
       break;
     case ST_QR:
-      k_qr<<<st.count, 256, 0, s>>>(x, j.qr + st.first);
+      k_qr<<<st.count, 256, st.smem, s>>>(x, j.qr + st.first, st.smem / 8);
       break;
     case ST_QAPPLY:
       k_qapply<<<st.count, 256, 0, s>>>(x, j.qapply + st.first);
       break;
     case ST_SVD:
-      k_svd<<<st.count, 256, svd_smem, s>>>(x, j.svd + st.first, st.first);
+      k_svd<<<st.count, 256, st.smem > 0 ? (size_t)st.smem : svd_smem, s>>>(x, j.svd + st.first, st.first);
+      break;
+    case ST_NORM:
+      k_norm<<<st.count, 256, norm_smem_bytes(), s>>>(x, j.norm + st.first);
       break;
     case ST_SCAN:
       k_scan<<<(st.count + 127) / 128, 128, 0, s>>>(x, j.scan + st.first, st.count);

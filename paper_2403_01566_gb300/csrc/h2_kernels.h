@@ -18,6 +18,7 @@ struct DeviceJobs {
   const QApplyJob* qapply = nullptr;
   const SvdJob* svd = nullptr;
   const ScanJob* scan = nullptr;
+  const NormJob* norm = nullptr;
 };
 
 cudaError_t kernels_init();

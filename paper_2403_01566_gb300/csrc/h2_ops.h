@@ -20,9 +20,11 @@ namespace h2 {
 // AR_K constants of the plan (identity matrices).
 enum Arena : int { AR_WS = 0, AR_X = 1, AR_Y = 2, AR_C = 3, AR_K = 4, AR_NONE = -1, AR_COUNT = 5 };
 
-// value = c + slot[s1] + slot[s2] (s1/s2 < 0: absent)
+// value = c + slot[s1] + slot[s2] (s1/s2 < 0: absent), then, if mc >= 0,
+// min(value, mc + slot[ms]) (ms < 0: absent).
 struct Dim {
   int c, s1, s2;
+  int mc = -1, ms = -1;
 };
 
 // address = base[arena] + off + slot[ds] * dm + slot[ds2] * dm2  (ds < 0: absent)
@@ -72,10 +74,13 @@ struct CopyJob {
 // diagonal the reflectors v (v_0 = 1 implicit) and tau[j] the factors.
 // If r.arena >= 0 the cols x cols upper-triangular R is also written row-major
 // to r (ldr); rows i >= q = min(rows, cols) are zero.
+// keep = 0: only R is needed (the reflectors may be left unwritten, and R may
+// differ from the full Householder R by the signs of its rows).
 struct QrJob {
   Ptr a, tau, r;
   int lda, ldr;
   Dim rows, cols;
+  int keep;
 };
 
 // out(rows x ncols) = H_0 H_1 ... H_{q-1} [Y; 0]  with the reflectors of a QrJob
@@ -109,6 +114,18 @@ struct SvdJob {
   int norm_idx;
 };
 
+// Spectral norm of the square matrix N (n x n, row-major): lambda_max(N^T N)
+// by Householder tridiagonalisation and Sturm-sequence bisection (accurate to
+// rounding relative to ||N||^2, unaffected by sign or rotation freedom of N's
+// factors).  Writes sqrt(lambda_max) to nrm[norm_idx], its inverse (0 for a
+// zero matrix) to scal[norm_idx].
+struct NormJob {
+  Ptr src;
+  int lds;
+  Dim n;
+  int norm_idx;
+};
+
 // slot[out + i] = sum_{j < i} slot[in[j]] for i = 0..count (count+1 outputs);
 // in[] lists slot indices (in the int index table at idx_off).
 struct ScanJob {
@@ -117,13 +134,14 @@ struct ScanJob {
   int out;
 };
 
-enum StageKind : int { ST_GEMM = 0, ST_COPY = 1, ST_QR = 2, ST_QAPPLY = 3, ST_SVD = 4, ST_SCAN = 5 };
+enum StageKind : int { ST_GEMM = 0, ST_COPY = 1, ST_QR = 2, ST_QAPPLY = 3, ST_SVD = 4, ST_SCAN = 5, ST_NORM = 6 };
 
 struct Stage {
   int kind;
   int64_t first;  // first job index in the kind's job array
   int count;      // number of jobs
   int tag;        // phase id, for profiling
+  int smem;       // dynamic shared memory of the launch (SVD stages: largest job)
 };
 
 // Kernel parameters common to all stages.

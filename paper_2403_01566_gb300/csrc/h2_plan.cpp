@@ -106,7 +106,9 @@ struct Builder {
   std::vector<QrJob> qj;
   std::vector<QApplyJob> qa;
   std::vector<SvdJob> sv;
+  int sv_maxr = 1, sv_maxc = 1;  // largest pending SVD job
   std::vector<ScanJob> sc;
+  std::vector<NormJob> nj;
 
   explicit Builder(Plan& p) : P(p) {}
   int64_t alloc(int64_t n) {
@@ -147,7 +149,7 @@ struct Builder {
       P.gout.push_back(o);
     }
     P.gterm.insert(P.gterm.end(), gt.begin(), gt.end());
-    P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag});
+    P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag, 0});
     go.clear();
     gt.clear();
   }
@@ -158,41 +160,63 @@ struct Builder {
   }
   void flush_copy(int tag) {
     if (cp.empty()) return;
-    P.stages.push_back(Stage{ST_COPY, (int64_t)P.copy.size(), (int)cp.size(), tag});
+    P.stages.push_back(Stage{ST_COPY, (int64_t)P.copy.size(), (int)cp.size(), tag, 0});
     P.copy.insert(P.copy.end(), cp.begin(), cp.end());
     cp.clear();
   }
-  void qr(Ptr a, int lda, Dim rows, Dim cols, Ptr tau, Ptr r, int ldr) {
-    qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols});
+  // QR job; maxr/maxc are the largest values rows/cols can take (shared-memory
+  // sizing of the stage); keep = 1 when a Q application needs the reflectors.
+  int qr_smem = 0;
+  void qr(Ptr a, int lda, Dim rows, Dim cols, Ptr tau, Ptr r, int ldr, int keep, int maxr, int maxc) {
+    qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep});
+    const int64_t cap = 6144;  // doubles, as in the kernel
+    int64_t need = (int64_t)maxr * maxc;
+    if (need > cap) need = 0;  // this job runs in global memory
+    (void)keep;
+    qr_smem = (int)std::max<int64_t>(qr_smem, need * 8);
   }
   void flush_qr(int tag) {
     if (qj.empty()) return;
-    P.stages.push_back(Stage{ST_QR, (int64_t)P.qr.size(), (int)qj.size(), tag});
+    P.stages.push_back(Stage{ST_QR, (int64_t)P.qr.size(), (int)qj.size(), tag, qr_smem});
     P.qr.insert(P.qr.end(), qj.begin(), qj.end());
     qj.clear();
+    qr_smem = 0;
   }
   void qapply(Ptr a, int lda, Ptr tau, Dim rows, Dim q, Ptr y, int ldy, Dim ncols, Ptr outp, int ldo) {
     qa.push_back(QApplyJob{a, tau, y, outp, lda, ldy, ldo, rows, q, ncols});
   }
   void flush_qapply(int tag) {
     if (qa.empty()) return;
-    P.stages.push_back(Stage{ST_QAPPLY, (int64_t)P.qap.size(), (int)qa.size(), tag});
+    P.stages.push_back(Stage{ST_QAPPLY, (int64_t)P.qap.size(), (int)qa.size(), tag, 0});
     P.qap.insert(P.qap.end(), qa.begin(), qa.end());
     qa.clear();
   }
   void svd(Ptr src, int lds, int trans, DimV rows, DimV cols, Ptr u, int ldu, Ptr sig, int mode, double tol,
            int tol_idx, int rank_slot, int cap, int norm_idx) {
     if (rows.max > SVD_MAXDIM || cols.max > SVD_MAXDIM) throw std::runtime_error("svd too large");
-    P.svd_maxrows = std::max(P.svd_maxrows, rows.max);
-    P.svd_maxcols = std::max(P.svd_maxcols, cols.max);
+    svd_size(rows.max, cols.max);
     sv.push_back(SvdJob{src, u, sig, lds, ldu, rows.d(), cols.d(), trans, mode, tol, tol_idx, rank_slot, cap,
                         norm_idx});
   }
+  void svd_size(int rows, int cols) {
+    sv_maxr = std::max(sv_maxr, rows);
+    sv_maxc = std::max(sv_maxc, cols);
+    P.svd_maxrows = std::max(P.svd_maxrows, rows);
+    P.svd_maxcols = std::max(P.svd_maxcols, cols);
+  }
   void flush_svd(int tag) {
     if (sv.empty()) return;
-    P.stages.push_back(Stage{ST_SVD, (int64_t)P.svd.size(), (int)sv.size(), tag});
+    const int smem = (int)(sizeof(double) * (size_t)(sv_maxr + 1) * sv_maxc);
+    P.stages.push_back(Stage{ST_SVD, (int64_t)P.svd.size(), (int)sv.size(), tag, smem});
     P.svd.insert(P.svd.end(), sv.begin(), sv.end());
     sv.clear();
+    sv_maxr = sv_maxc = 1;
+  }
+  void flush_norm(int tag) {
+    if (nj.empty()) return;
+    P.stages.push_back(Stage{ST_NORM, (int64_t)P.norm.size(), (int)nj.size(), tag, 0});
+    P.norm.insert(P.norm.end(), nj.begin(), nj.end());
+    nj.clear();
   }
   void scan(const std::vector<int>& in_slots, int out_first) {
     sc.push_back(ScanJob{(int)P.idx.size(), (int)in_slots.size(), out_first});
@@ -200,7 +224,7 @@ struct Builder {
   }
   void flush_scan(int tag) {
     if (sc.empty()) return;
-    P.stages.push_back(Stage{ST_SCAN, (int64_t)P.scan.size(), (int)sc.size(), tag});
+    P.stages.push_back(Stage{ST_SCAN, (int64_t)P.scan.size(), (int)sc.size(), tag, 0});
     P.scan.insert(P.scan.end(), sc.begin(), sc.end());
     sc.clear();
   }
@@ -950,8 +974,10 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
           // W = R^T (column-major R)
           B.copy(J.f1.R.p, J.f1.R.ld, PT(AR_WS, s.W1), J.f1.rows_r, J.f1.m.d(), DC(J.f1.rows_r), 1);
           B.copy(J.f2.R.p, J.f2.R.ld, PT(AR_WS, s.W2), J.f2.rows_r, J.f2.m.d(), DC(J.f2.rows_r), 1);
-          B.qr(PT(AR_WS, s.W1), J.f1.rows_r, DC(J.f1.rows_r), J.f1.m.d(), PT(AR_WS, s.tau1), PT(AR_WS, s.rho1), m1);
-          B.qr(PT(AR_WS, s.W2), J.f2.rows_r, DC(J.f2.rows_r), J.f2.m.d(), PT(AR_WS, s.tau2), PT(AR_WS, s.rho2), m2);
+          B.qr(PT(AR_WS, s.W1), J.f1.rows_r, DC(J.f1.rows_r), J.f1.m.d(), PT(AR_WS, s.tau1), PT(AR_WS, s.rho1), m1, 1,
+               J.f1.rows_r, m1);
+          B.qr(PT(AR_WS, s.W2), J.f2.rows_r, DC(J.f2.rows_r), J.f2.m.d(), PT(AR_WS, s.tau2), PT(AR_WS, s.rho2), m2, 1,
+               J.f2.rows_r, m2);
         } else {
           s.W1 = B.alloc((int64_t)J.f1.rows_r * (m1 + m2));
           s.tau1 = B.alloc(m1 + m2);
@@ -960,7 +986,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
           B.copy(J.f2.R.p, J.f2.R.ld, pdyn(PT(AR_WS, s.W1 + (int64_t)J.f1.m.c * J.f1.rows_r), J.f1.m.s, J.f1.rows_r),
                  J.f1.rows_r, J.f2.m.d(), DC(J.f1.rows_r), 1);
           const Dim mm = merged_width(J.f1.m, J.f2.m);
-          B.qr(PT(AR_WS, s.W1), J.f1.rows_r, DC(J.f1.rows_r), mm, PT(AR_WS, s.tau1), PT(AR_WS, s.rho1), m1 + m2);
+          B.qr(PT(AR_WS, s.W1), J.f1.rows_r, DC(J.f1.rows_r), mm, PT(AR_WS, s.tau1), PT(AR_WS, s.rho1), m1 + m2, 1,
+               J.f1.rows_r, m1 + m2);
         }
         s.Gc = B.alloc((int64_t)(J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t) * AGGC);
         s.Wc = B.alloc((int64_t)(J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t) * (m1 + m2));
@@ -1024,7 +1051,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         const int m1 = J.f1.m.max, m2 = J.f2.m.max;
         const int rows = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
         const Dim wd = merged_width(J.f1.m, J.f2.m);
-        B.qr(PT(AR_WS, s.Wc), rows, DC(rows), wd, PT(AR_WS, s.tauc), PT(AR_WS, s.rhoc), AGGC);
+        B.qr(PT(AR_WS, s.Wc), rows, DC(rows), wd, PT(AR_WS, s.tauc), PT(AR_WS, s.rhoc), AGGC, 0, rows,
+             J.f1.m.max + J.f2.m.max);
       }
       B.flush_qr(TAG_AGG);
       for (size_t j = 0; j < jobs.size(); ++j) {
@@ -1034,9 +1062,13 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         // M = rho_c^T ((m1+m2) x (m1+m2)); rows and cols are the merged width
         const Dim wd = merged_width(J.f1.m, J.f2.m);
         if (m1 + m2 > SVD_MAXDIM) throw std::runtime_error("agglomeration svd too large");
-        P.svd_maxrows = std::max(P.svd_maxrows, m1 + m2);
-        P.svd_maxcols = std::max(P.svd_maxcols, m1 + m2);
-        B.sv.push_back(SvdJob{PT(AR_WS, s.rhoc), PT(AR_WS, s.U), PT(AR_WS, s.sig), AGGC, AGGC, wd, wd, 1, 2, J.rel,
+        // M = rho_c^T (width x q), q = min(width, rows of Gc): the rows of rho_c
+        // beyond q are zero
+        const int gc_rows = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
+        Dim qcols = wd;
+        qcols.mc = gc_rows;
+        B.svd_size(m1 + m2, std::min(m1 + m2, gc_rows));
+        B.sv.push_back(SvdJob{PT(AR_WS, s.rhoc), PT(AR_WS, s.U), PT(AR_WS, s.sig), AGGC, AGGC, wd, qcols, 1, 2, J.rel,
                               PARAM_TOL_AGG, outs[j].m.s, AGGM, -1});
       }
       B.flush_svd(TAG_AGG);
@@ -1119,8 +1151,10 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       scr[i][3] = B.alloc(m);
       B.copy(F.f.R.p, F.f.R.ld, PT(AR_WS, scr[i][0]), F.f.rows_r, F.f.m.d(), DC(F.f.rows_r), 1);
       B.copy(F.f.L.p, F.f.L.ld, PT(AR_WS, scr[i][1]), F.f.rows_t, F.f.m.d(), DC(F.f.rows_t), 1);
-      B.qr(PT(AR_WS, scr[i][0]), F.f.rows_r, DC(F.f.rows_r), F.f.m.d(), PT(AR_WS, scr[i][2]), PT(AR_WS, F.rhoR), MB);
-      B.qr(PT(AR_WS, scr[i][1]), F.f.rows_t, DC(F.f.rows_t), F.f.m.d(), PT(AR_WS, scr[i][3]), PT(AR_WS, F.rhoL), MB);
+      B.qr(PT(AR_WS, scr[i][0]), F.f.rows_r, DC(F.f.rows_r), F.f.m.d(), PT(AR_WS, scr[i][2]), PT(AR_WS, F.rhoR), MB, 0,
+           F.f.rows_r, m);
+      B.qr(PT(AR_WS, scr[i][1]), F.f.rows_t, DC(F.f.rows_t), F.f.m.d(), PT(AR_WS, scr[i][3]), PT(AR_WS, F.rhoL), MB, 0,
+           F.f.rows_t, m);
     }
     B.flush_copy(TAG_COND);
     B.flush_qr(TAG_COND);
@@ -1142,145 +1176,203 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     B.flush_gemm(TAG_COND);
     for (size_t i = 0; i < fin.size(); ++i) {
       Final& F = fin[i];
-      B.svd(PT(AR_WS, nm[i]), MB, 0, F.f.m.s >= 0 ? dvs(F.f.m.s, F.f.m.max) : dv(F.f.m.c),
-            F.f.m.s >= 0 ? dvs(F.f.m.s, F.f.m.max) : dv(F.f.m.c), NONE(), 0, NONE(), 4, 0.0, -1, -1, 0, F.nidx);
+      B.nj.push_back(NormJob{PT(AR_WS, nm[i]), MB, F.f.m.d(), F.nidx});
     }
-    B.flush_svd(TAG_COND);
+    B.flush_norm(TAG_COND);
     (void)mark;
     (void)mark2;
   }
 
   // --------------------------------------- 12. adaptive cluster bases ----
   // row*(t): final admissible blocks whose row cluster is t or an ancestor.
-  auto build_basis = [&](bool rowside) {
-    const Tree& T = rowside ? TI : TK;
-    const int tag = rowside ? TAG_ROWB : TAG_COLB;
-    const int64_t offBasis = rowside ? P.c_off_V : P.c_off_W;
-    const int64_t offTrans = rowside ? P.c_off_E : P.c_off_F;
-    std::vector<std::vector<int>> own(T.ncl), star(T.ncl);
+  // The row and the column basis are independent: their levels run in the
+  // same launches (twice the jobs per stage).
+  struct Side {
+    bool rowside;
+    const Tree* T;
+    int tag;
+    int64_t offBasis, offTrans;
+    std::vector<std::vector<int>> star;
+    std::vector<int> rank;
+    std::map<std::pair<int, int>, int64_t> lam;  // Lambda-hat_{c,b} = V_c^* L_b|_c (KP x MB)
+    // per level
+    std::vector<int> cl, offslot, wmax;
+    std::vector<int64_t> panel, rbuf, ubuf, tbuf;
+  };
+  auto make_basis_side = [&](bool rowside) {
+    Side S;
+    S.rowside = rowside;
+    S.T = rowside ? &TI : &TK;
+    S.tag = rowside ? TAG_ROWB : TAG_COLB;
+    S.offBasis = rowside ? P.c_off_V : P.c_off_W;
+    S.offTrans = rowside ? P.c_off_E : P.c_off_F;
+    const Tree& T = *S.T;
+    std::vector<std::vector<int>> own(T.ncl);
+    S.star.resize(T.ncl);
     for (size_t i = 0; i < fin.size(); ++i) own[rowside ? fin[i].t : fin[i].r].push_back((int)i);
     for (int c = 0; c < T.ncl; ++c) {
-      if (c > 0) star[c] = star[Tree::parent(c)];
-      star[c].insert(star[c].end(), own[c].begin(), own[c].end());
+      if (c > 0) S.star[c] = S.star[Tree::parent(c)];
+      S.star[c].insert(S.star[c].end(), own[c].begin(), own[c].end());
     }
-    std::vector<int> rank(T.ncl, -1);
-    for (int c = 0; c < T.ncl; ++c) rank[c] = B.slot(0);
-    (rowside ? P.rank_row_slot : P.rank_col_slot) = rank;
-    // Lambda-hat_{c,b} = V_c^* L_b|_c  (KP x MB each)
-    std::map<std::pair<int, int>, int64_t> lam;
-    auto fac_rows = [&](const Final& F) { return rowside ? F.f.L : F.f.R; };
-    auto blk_cluster = [&](const Final& F) { return rowside ? F.t : F.r; };
-    auto rho = [&](const Final& F) { return rowside ? F.rhoR : F.rhoL; };
-    auto Gcond = [&](const Final& F) { return rowside ? F.Gc : F.Gcc; };
-    const double tol_mult = 1.0;
-    for (int l = D; l >= 0; --l) {
-      const int64_t mark = B.ws;
-      std::vector<int> cl;
-      for (int c = Tree::first(l); c < Tree::first(l + 1); ++c)
-        if (!star[c].empty()) cl.push_back(c);
-      // panel widths: prefix sums of the factor widths
-      std::vector<int> offslot(T.ncl, -1);
-      std::vector<int64_t> panel(T.ncl, -1), rbuf(T.ncl, -1), ubuf(T.ncl, -1), tbuf(T.ncl, -1);
-      std::vector<int> wmax(T.ncl, 0);
-      for (int c : cl) {
-        std::vector<int> in;
-        for (int b : star[c]) {
-          const Final& F = fin[b];
-          in.push_back(F.f.m.s >= 0 ? F.f.m.s : B.slot(F.f.m.c));
-          wmax[c] += F.f.m.max;
-        }
-        offslot[c] = (int)P.slot_init.size();
-        for (size_t i = 0; i <= in.size(); ++i) B.slot(0);
-        B.scan(in, offslot[c]);
-      }
-      B.flush_scan(tag);
-      for (int c : cl) {
-        const int rows = T.leaf(c) ? T.size[c] : 2 * KP;
-        panel[c] = B.alloc((int64_t)rows * wmax[c]);
-        const int n = T.leaf(c) ? T.size[c] : 2 * KP;
-        rbuf[c] = B.alloc((int64_t)n * n);
-        ubuf[c] = B.alloc((int64_t)n * n);
-        tbuf[c] = B.alloc(n);
-        const int lev = T.level[c];
-        for (size_t i = 0; i < star[c].size(); ++i) {
-          const Final& F = fin[star[c][i]];
-          const int tb = blk_cluster(F);
-          const double w = std::pow(theta, -0.5 * (lev - T.level[tb]));  // 1/omega up to 1/||G||
-          Ptr dst = pdyn(PT(AR_WS, panel[c]), offslot[c] + (int)i, 1);
-          if (T.leaf(c)) {
-            // leaf: omega^{-1} G^c_b restricted to the rows of c
-            const int64_t r0 = T.off[c] - T.off[tb];
-            B.copy(PT(AR_WS, Gcond(F) + r0 * MB), MB, dst, wmax[c], DC(T.size[c]), F.f.m.d(), 0, w, F.nidx);
-          } else {
-            // inner: omega^{-1} [Lhat_{c1,b}; Lhat_{c2,b}] rho_b^T
-            for (int h = 0; h < 2; ++h) {
-              const int ch = Tree::child(c, h);
-              Ptr d2 = h == 0 ? dst : pdyn(dst, rank[Tree::child(c, 0)], wmax[c]);
-              B.out(d2, wmax[c], DS(rank[ch]), F.f.m.d(), 0);
-              B.term2(mref(PT(AR_WS, lam.at({ch, star[c][i]})), MB), mref(PT(AR_WS, rho(F)), MB, 1), F.f.m.d(), w,
-                      F.nidx);
-            }
-          }
-        }
-      }
-      B.flush_all(tag);
-      // QR of the panel (column-major view: width x rows), then Jacobi SVD of R^T
-      for (int c : cl) {
-        const int n = T.leaf(c) ? T.size[c] : 2 * KP;
-        Dim rows_d = T.leaf(c) ? DC(T.size[c]) : DSS(rank[Tree::child(c, 0)], rank[Tree::child(c, 1)]);
-        const int nsl = offslot[c] + (int)star[c].size();  // total width slot
-        B.qr(PT(AR_WS, panel[c]), wmax[c], DS(nsl), rows_d, PT(AR_WS, tbuf[c]), PT(AR_WS, rbuf[c]), n);
-      }
-      B.flush_qr(tag);
-      for (int c : cl) {
-        const int n = T.leaf(c) ? T.size[c] : 2 * KP;
-        Dim rows_d = T.leaf(c) ? DC(T.size[c]) : DSS(rank[Tree::child(c, 0)], rank[Tree::child(c, 1)]);
-        P.svd_maxrows = std::max(P.svd_maxrows, n);
-        P.svd_maxcols = std::max(P.svd_maxcols, n);
-        B.sv.push_back(SvdJob{PT(AR_WS, rbuf[c]), PT(AR_WS, ubuf[c]), NONE(), n, n, rows_d, rows_d, 1, 1, tol_mult,
-                              PARAM_TOL_BASIS, rank[c], KP, -1});
-      }
-      B.flush_svd(tag);
-      // new basis: leaves V_c = U[:, :k_c]; inner E_{c1}, E_{c2} = blocks of U[:, :k_c]
-      for (int c : cl) {
-        const int n = T.leaf(c) ? T.size[c] : 2 * KP;
-        if (T.leaf(c)) {
-          B.copy(PT(AR_WS, ubuf[c]), n, PT(AR_C, offBasis + (int64_t)T.off[c] * KP), KP, DC(T.size[c]), DS(rank[c]), 0);
-        } else {
-          const int c1 = Tree::child(c, 0), c2 = Tree::child(c, 1);
-          B.copy(PT(AR_WS, ubuf[c]), n, PT(AR_C, offTrans + (int64_t)c1 * KP * KP), KP, DS(rank[c1]), DS(rank[c]), 0);
-          B.copy(pdyn(PT(AR_WS, ubuf[c]), rank[c1], n), n, PT(AR_C, offTrans + (int64_t)c2 * KP * KP), KP,
-                 DS(rank[c2]), DS(rank[c]), 0);
-        }
-      }
-      B.flush_copy(tag);
-      B.ws = mark;
-      // projection climb: Lhat_{c,b} = V_c^* L_b|_c (leaf) or E_{c1}^* Lhat_{c1,b} + E_{c2}^* Lhat_{c2,b}
-      for (int c : cl) {
-        for (int b : star[c]) {
-          const Final& F = fin[b];
-          const int64_t o = B.alloc((int64_t)KP * MB);
-          lam[{c, b}] = o;
-          B.out(PT(AR_WS, o), MB, DS(rank[c]), F.f.m.d(), 0);
-          if (T.leaf(c)) {
-            const int tb = blk_cluster(F);
-            MRef Lr = rows_of(fac_rows(F), T.off[c] - T.off[tb]);
-            B.term2(mref(PT(AR_C, offBasis + (int64_t)T.off[c] * KP), KP, 1), Lr, DC(T.size[c]));
-          } else {
-            for (int h = 0; h < 2; ++h) {
-              const int ch = Tree::child(c, h);
-              B.term2(mref(PT(AR_C, offTrans + (int64_t)ch * KP * KP), KP, 1), mref(PT(AR_WS, lam.at({ch, b})), MB),
-                      DS(rank[ch]));
-            }
-          }
-        }
-      }
-      B.flush_gemm(tag);
-    }
-    return lam;
+    S.rank.assign(T.ncl, -1);
+    for (int c = 0; c < T.ncl; ++c) S.rank[c] = B.slot(0);
+    (rowside ? P.rank_row_slot : P.rank_col_slot) = S.rank;
+    return S;
   };
-  auto lamR = build_basis(true);
-  auto lamC = build_basis(false);
+  Side SR = make_basis_side(true), SC = make_basis_side(false);
+  auto fac_rows = [&](const Side& S, const Final& F) { return S.rowside ? F.f.L : F.f.R; };
+  auto blk_cluster = [&](const Side& S, const Final& F) { return S.rowside ? F.t : F.r; };
+  auto rho = [&](const Side& S, const Final& F) { return S.rowside ? F.rhoR : F.rhoL; };
+  auto Gcond = [&](const Side& S, const Final& F) { return S.rowside ? F.Gc : F.Gcc; };
+  const double tol_mult = 1.0;
+  // phase 0: panel widths (prefix sums of the factor widths)
+  auto ph_scan = [&](Side& S, int l) {
+    const Tree& T = *S.T;
+    S.cl.clear();
+    for (int c = Tree::first(l); c < Tree::first(l + 1); ++c)
+      if (!S.star[c].empty()) S.cl.push_back(c);
+    S.offslot.assign(T.ncl, -1);
+    S.wmax.assign(T.ncl, 0);
+    S.panel.assign(T.ncl, -1);
+    S.rbuf.assign(T.ncl, -1);
+    S.ubuf.assign(T.ncl, -1);
+    S.tbuf.assign(T.ncl, -1);
+    for (int c : S.cl) {
+      std::vector<int> in;
+      for (int b : S.star[c]) {
+        const Final& F = fin[b];
+        in.push_back(F.f.m.s >= 0 ? F.f.m.s : B.slot(F.f.m.c));
+        S.wmax[c] += F.f.m.max;
+      }
+      S.offslot[c] = (int)P.slot_init.size();
+      for (size_t i = 0; i <= in.size(); ++i) B.slot(0);
+      B.scan(in, S.offslot[c]);
+    }
+  };
+  // phase 1: weighted panels
+  auto ph_panel = [&](Side& S) {
+    const Tree& T = *S.T;
+    for (int c : S.cl) {
+      const int n = T.leaf(c) ? T.size[c] : 2 * KP;
+      S.panel[c] = B.alloc((int64_t)n * S.wmax[c]);
+      S.rbuf[c] = B.alloc((int64_t)n * n);
+      S.ubuf[c] = B.alloc((int64_t)n * n);
+      S.tbuf[c] = B.alloc(n);
+      const int lev = T.level[c];
+      for (size_t i = 0; i < S.star[c].size(); ++i) {
+        const Final& F = fin[S.star[c][i]];
+        const int tb = blk_cluster(S, F);
+        const double w = std::pow(theta, -0.5 * (lev - T.level[tb]));  // 1/omega up to 1/||G||
+        Ptr dst = pdyn(PT(AR_WS, S.panel[c]), S.offslot[c] + (int)i, 1);
+        if (T.leaf(c)) {
+          // leaf: omega^{-1} G^c_b restricted to the rows of c
+          const int64_t r0 = T.off[c] - T.off[tb];
+          B.copy(PT(AR_WS, Gcond(S, F) + r0 * MB), MB, dst, S.wmax[c], DC(T.size[c]), F.f.m.d(), 0, w, F.nidx);
+        } else {
+          // inner: omega^{-1} [Lhat_{c1,b}; Lhat_{c2,b}] rho_b^T
+          for (int h = 0; h < 2; ++h) {
+            const int ch = Tree::child(c, h);
+            Ptr d2 = h == 0 ? dst : pdyn(dst, S.rank[Tree::child(c, 0)], S.wmax[c]);
+            B.out(d2, S.wmax[c], DS(S.rank[ch]), F.f.m.d(), 0);
+            B.term2(mref(PT(AR_WS, S.lam.at({ch, S.star[c][i]})), MB), mref(PT(AR_WS, rho(S, F)), MB, 1), F.f.m.d(),
+                    w, F.nidx);
+          }
+        }
+      }
+    }
+  };
+  auto rows_dim = [&](const Side& S, int c) {
+    const Tree& T = *S.T;
+    return T.leaf(c) ? DC(T.size[c]) : DSS(S.rank[Tree::child(c, 0)], S.rank[Tree::child(c, 1)]);
+  };
+  // phase 2: QR of the panel (column-major view: width x rows)
+  auto ph_qr = [&](Side& S) {
+    const Tree& T = *S.T;
+    for (int c : S.cl) {
+      const int n = T.leaf(c) ? T.size[c] : 2 * KP;
+      const int nsl = S.offslot[c] + (int)S.star[c].size();  // total width slot
+      B.qr(PT(AR_WS, S.panel[c]), S.wmax[c], DS(nsl), rows_dim(S, c), PT(AR_WS, S.tbuf[c]), PT(AR_WS, S.rbuf[c]), n,
+           0, S.wmax[c], n);
+    }
+  };
+  // phase 3: Jacobi SVD of R^T with the truncation rule
+  auto ph_svd = [&](Side& S) {
+    const Tree& T = *S.T;
+    for (int c : S.cl) {
+      const int n = T.leaf(c) ? T.size[c] : 2 * KP;
+      const Dim rows_d = rows_dim(S, c);
+      B.svd_size(n, n);
+      Dim qcols = rows_d;  // M = R^T (rows x q), q = min(rows, panel width)
+      qcols.mc = 0;
+      qcols.ms = S.offslot[c] + (int)S.star[c].size();
+      B.sv.push_back(SvdJob{PT(AR_WS, S.rbuf[c]), PT(AR_WS, S.ubuf[c]), NONE(), n, n, rows_d, qcols, 1, 1, tol_mult,
+                            PARAM_TOL_BASIS, S.rank[c], KP, -1});
+    }
+  };
+  // phase 4: new basis: leaves V_c = U[:, :k_c]; inner E_{c1}, E_{c2} = blocks of U[:, :k_c]
+  auto ph_store = [&](Side& S) {
+    const Tree& T = *S.T;
+    for (int c : S.cl) {
+      const int n = T.leaf(c) ? T.size[c] : 2 * KP;
+      if (T.leaf(c)) {
+        B.copy(PT(AR_WS, S.ubuf[c]), n, PT(AR_C, S.offBasis + (int64_t)T.off[c] * KP), KP, DC(T.size[c]),
+               DS(S.rank[c]), 0);
+      } else {
+        const int c1 = Tree::child(c, 0), c2 = Tree::child(c, 1);
+        B.copy(PT(AR_WS, S.ubuf[c]), n, PT(AR_C, S.offTrans + (int64_t)c1 * KP * KP), KP, DS(S.rank[c1]),
+               DS(S.rank[c]), 0);
+        B.copy(pdyn(PT(AR_WS, S.ubuf[c]), S.rank[c1], n), n, PT(AR_C, S.offTrans + (int64_t)c2 * KP * KP), KP,
+               DS(S.rank[c2]), DS(S.rank[c]), 0);
+      }
+    }
+  };
+  // phase 5: projection climb: Lhat_{c,b} = V_c^* L_b|_c (leaf) or E_{c1}^* Lhat_{c1,b} + E_{c2}^* Lhat_{c2,b}
+  auto ph_climb = [&](Side& S) {
+    const Tree& T = *S.T;
+    for (int c : S.cl) {
+      for (int b : S.star[c]) {
+        const Final& F = fin[b];
+        const int64_t o = B.alloc((int64_t)KP * MB);
+        S.lam[{c, b}] = o;
+        B.out(PT(AR_WS, o), MB, DS(S.rank[c]), F.f.m.d(), 0);
+        if (T.leaf(c)) {
+          const int tb = blk_cluster(S, F);
+          MRef Lr = rows_of(fac_rows(S, F), T.off[c] - T.off[tb]);
+          B.term2(mref(PT(AR_C, S.offBasis + (int64_t)T.off[c] * KP), KP, 1), Lr, DC(T.size[c]));
+        } else {
+          for (int h = 0; h < 2; ++h) {
+            const int ch = Tree::child(c, h);
+            B.term2(mref(PT(AR_C, S.offTrans + (int64_t)ch * KP * KP), KP, 1), mref(PT(AR_WS, S.lam.at({ch, b})), MB),
+                    DS(S.rank[ch]));
+          }
+        }
+      }
+    }
+  };
+  for (int l = D; l >= 0; --l) {
+    const int64_t mark = B.ws;
+    ph_scan(SR, l);
+    ph_scan(SC, l);
+    B.flush_scan(TAG_ROWB);
+    ph_panel(SR);
+    ph_panel(SC);
+    B.flush_all(TAG_ROWB);
+    ph_qr(SR);
+    ph_qr(SC);
+    B.flush_qr(TAG_ROWB);
+    ph_svd(SR);
+    ph_svd(SC);
+    B.flush_svd(TAG_ROWB);
+    ph_store(SR);
+    ph_store(SC);
+    B.flush_copy(TAG_ROWB);
+    B.ws = mark;  // panels and factorizations of this level are free again
+    ph_climb(SR);
+    ph_climb(SC);
+    B.flush_gemm(TAG_ROWB);
+  }
+  auto& lamR = SR.lam;
+  auto& lamC = SC.lam;
 
   // --------------------------------------------------- 13. couplings ----
   // S_b = (V_t^* L_b) (W_r^* R_b)^*
@@ -1298,6 +1390,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   P.stats["gemm_outputs"] = P.gout.size();
   P.stats["gemm_terms"] = P.gterm.size();
   P.stats["svd_jobs"] = P.svd.size();
+  P.stats["norm_jobs"] = P.norm.size();
   P.stats["qr_jobs"] = P.qr.size();
   P.stats["ws_bytes"] = P.ws_len * 8;
   return plan;

@@ -43,6 +43,7 @@ struct Plan {
   std::vector<QApplyJob> qap;
   std::vector<SvdJob> svd;
   std::vector<ScanJob> scan;
+  std::vector<NormJob> norm;
   std::vector<int> idx;
   std::vector<int> slot_init;
   std::vector<double> konst;     // AR_K contents

@@ -172,7 +172,7 @@ def mul(A: H2Matrix, B: H2Matrix, eps: float, max_rank: int = 0, theta: float = 
 
 def mul_profile(A: H2Matrix, B: H2Matrix, eps: float, prof, max_rank: int = 0, stream=None) -> H2Matrix:
     """h2_mul_profile: the product with per-kernel-kind device times and work in `prof`
-    (an array of 7 KernelProf)."""
+    (an array of 8 KernelProf)."""
     o = MulOpts()
     o.theta, o.max_rank, o.precision, o.sync = 0.0, int(max_rank), 0, 1
     o.stream = stream
