@@ -227,7 +227,6 @@ __device__ double block_sum(double v, double* red) {
 // one warp per trailing column; `a` is global or shared memory.
 __device__ void householder_cols(double* a, int lda, int rows, int cols, double* tau, double* red, double* sh) {
   const int q = min(rows, cols);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = 0; j < q; ++j) {
     double* col = a + (int64_t)j * lda;
     double s2 = 0.0;
@@ -251,14 +250,26 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
     if (t != 0.0) {
       for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) col[i] *= sc;
       __syncthreads();
-      for (int c = j + 1 + warp; c < cols; c += nw) {
+      // trailing columns: teams of ts lanes per column (short columns use small
+      // teams so that the FP64 shuffle reduction stays short)
+      const int len = rows - j - 1;
+      int ts = 32;
+      while (ts > 1 && ts * 8 > len) ts >>= 1;
+      const int nteam = blockDim.x / ts, team = threadIdx.x / ts, tl = threadIdx.x % ts;
+      for (int c0 = j + 1; c0 < cols; c0 += nteam) {
+        const int c = c0 + team;
+        double p = 0.0, cj = 0.0;
         double* cc = a + (int64_t)c * lda;
-        double p = 0.0;
-        for (int i = j + 1 + lane; i < rows; i += 32) p = fma(col[i], cc[i], p);
-        p = warp_sum(p);
-        const double w = t * (cc[j] + p);
-        if (lane == 0) cc[j] -= w;
-        for (int i = j + 1 + lane; i < rows; i += 32) cc[i] = fma(-w, col[i], cc[i]);
+        if (c < cols) {
+          cj = cc[j];  // read by every lane before the shuffle (lane 0 writes it below)
+          for (int i = j + 1 + tl; i < rows; i += ts) p = fma(col[i], cc[i], p);
+        }
+        for (int o = ts >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (c < cols) {
+          const double w = t * (cj + p);
+          if (tl == 0) cc[j] -= w;
+          for (int i = j + 1 + tl; i < rows; i += ts) cc[i] = fma(-w, col[i], cc[i]);
+        }
       }
     }
     __syncthreads();
@@ -357,13 +368,28 @@ __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, 
 // product plus the rotation.
 constexpr int SVD_MAXSWEEP = 60;
 
+// Round-robin (circle method) pairing of ce (even) columns: in round rnd, pair
+// p matches columns i < j; over ce-1 rounds every pair meets once.
+__device__ __forceinline__ int svd_pair_a(int rnd, int p, int ce) { return p == 0 ? rnd : (rnd + p) % (ce - 1); }
+__device__ __forceinline__ int svd_pair_b(int rnd, int p, int ce) {
+  return p == 0 ? ce - 1 : (rnd - p + ce - 1) % (ce - 1);
+}
+__device__ __forceinline__ int svd_pair_i(int rnd, int p, int ce) {
+  return min(svd_pair_a(rnd, p, ce), svd_pair_b(rnd, p, ce));
+}
+__device__ __forceinline__ int svd_pair_j(int rnd, int p, int ce) {
+  return max(svd_pair_a(rnd, p, ce), svd_pair_b(rnd, p, ce));
+}
+
 __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, const SvdJob* __restrict__ jobs,
-                                             int64_t first) {
+                                             int64_t first, int smem_doubles) {
   const ExecCtx& x = *px;
   extern __shared__ double sm[];
   __shared__ int rotated;
   __shared__ int nrot;
+  __shared__ int nround;
   __shared__ double nrm2[SVD_MAXDIM];
+  __shared__ double gam[SVD_MAXDIM / 2 + 1], rc[SVD_MAXDIM / 2 + 1], rs[SVD_MAXDIM / 2 + 1];
   __shared__ double snorm[SVD_MAXDIM];
   __shared__ int spos[SVD_MAXDIM];
   __shared__ double s_fro;
@@ -387,14 +413,22 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
     }
     return;
   }
-  const int ldm = rows + 1;
-  double* M = sm;  // column c at M + c*ldm
-  const double* S = ptrv(J.src, x);
-  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-    int r = e / cols, c = e % cols;
-    M[c * ldm + r] = J.trans ? S[(int64_t)c * J.lds + r] : S[(int64_t)r * J.lds + c];
+  // M in shared memory when it fits the launch, else in place in the source
+  // (only for transposed sources, whose rows are M's columns; the planner
+  // passes scratch copies that are not needed afterwards)
+  double* S = ptrv(J.src, x);
+  const bool in_smem = (int64_t)(rows + 1) * cols <= smem_doubles || !J.trans;
+  const int ldm = in_smem ? rows + 1 : J.lds;
+  double* M = in_smem ? sm : S;  // column c at M + c*ldm
+  if (in_smem)
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      int r = e / cols, c = e % cols;
+      M[c * ldm + r] = J.trans ? S[(int64_t)c * J.lds + r] : S[(int64_t)r * J.lds + c];
+    }
+  if (threadIdx.x == 0) {
+    nrot = 0;
+    nround = 0;
   }
-  if (threadIdx.x == 0) nrot = 0;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   // exact squared column norms (one warp per column)
@@ -418,76 +452,84 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
   const double tiny2 = s_fro * 7.888609052210118e-31;
   const int ce = cols + (cols & 1);
   const int npairs = ce / 2;
-  int ts = 32;
-  while (ts > 1 && ts * npairs > (int)blockDim.x) ts >>= 1;
-  const int team = threadIdx.x / ts, tl = threadIdx.x % ts;
   const double tol = 2.5e-15;
+  // teams of ts lanes per pair: at least 8 rows per lane, at most a warp
+  int ts = 32;
+  while (ts > 1 && ts * 8 > rows) ts >>= 1;
+  const int nteam = blockDim.x / ts, team = threadIdx.x / ts, tl = threadIdx.x % ts;
   int sweep = 0;
   for (; sweep < SVD_MAXSWEEP; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int rnd = 0; rnd < ce - 1; ++rnd) {
-      int i = -1, j = -1;
-      if (team < npairs) {
-        if (team == 0) {
-          i = rnd;
-          j = ce - 1;
-        } else {
-          i = (rnd + team) % (ce - 1);
-          j = (rnd - team + ce - 1) % (ce - 1);
+      // phase A: dot products gamma_p = m_i . m_j of the round's pairs
+      for (int p0 = 0; p0 < npairs; p0 += nteam) {
+        const int p = p0 + team;
+        double ga = 0.0, g2 = 0.0;
+        if (p < npairs) {
+          const int i = svd_pair_i(rnd, p, ce), j = svd_pair_j(rnd, p, ce);
+          if (j < cols) {
+            const double* mi = M + i * ldm;
+            const double* mj = M + j * ldm;
+            int r = tl;
+            for (; r + ts < rows; r += 2 * ts) {
+              ga = fma(mi[r], mj[r], ga);
+              g2 = fma(mi[r + ts], mj[r + ts], g2);
+            }
+            if (r < rows) ga = fma(mi[r], mj[r], ga);
+          }
         }
-        if (i > j) {
-          const int t = i;
-          i = j;
-          j = t;
-        }
-      }
-      const bool valid = team < npairs && j < cols;
-      double ga = 0.0;
-      if (valid) {
-        const double* mi = M + i * ldm;
-        const double* mj = M + j * ldm;
-        double g2 = 0.0;
-        int r = tl;
-        for (; r + ts < rows; r += 2 * ts) {
-          ga = fma(mi[r], mj[r], ga);
-          g2 = fma(mi[r + ts], mj[r + ts], g2);
-        }
-        if (r < rows) ga = fma(mi[r], mj[r], ga);
         ga += g2;
+        for (int o = ts >> 1; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        if (p < npairs && tl == 0) gam[p] = ga;
       }
-      for (int o = ts >> 1; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
-      // rotation parameters on the team leader only (FP64 sqrt/div are long
-      // instruction sequences), broadcast to the team
-      double c = 1.0, sn = 0.0;
-      int rot = 0;
-      if (valid && tl == 0) {
-        const double al = nrm2[i], be = nrm2[j];
-        // |ga| > tol * sqrt(al * be), in squared form
-        if (ga != 0.0 && al > tiny2 && be > tiny2 && ga * ga > (tol * tol) * al * be) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          c = rsqrt(1.0 + t * t);
-          sn = c * t;
-          rot = 1;
-          nrm2[i] = fmax(al - t * ga, 0.0);
-          nrm2[j] = be + t * ga;
+      __syncthreads();
+      // phase B: rotation parameters, one lane per pair (the FP64 divide and
+      // square-root sequences run 32 pairs wide)
+      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        const int i = svd_pair_i(rnd, p, ce), j = svd_pair_j(rnd, p, ce);
+        double c = 1.0, sn = 0.0;
+        int rot = 0;
+        if (j < cols) {
+          const double ga = gam[p], al = nrm2[i], be = nrm2[j];
+          // |ga| > tol * sqrt(al * be), in squared form
+          if (ga != 0.0 && al > tiny2 && be > tiny2 && ga * ga > (tol * tol) * al * be) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = rsqrt(1.0 + t * t);
+            sn = c * t;
+            rot = 1;
+            nrm2[i] = fmax(al - t * ga, 0.0);
+            nrm2[j] = be + t * ga;
+          }
+        }
+        rc[p] = c;
+        rs[p] = rot ? sn : 0.0;
+        if (rot) {
           rotated = 1;
+          nround = 1;
           atomicAdd(&nrot, 1);
         }
       }
-      const int leader = (threadIdx.x & 31) & ~(ts - 1);
-      rot = __shfl_sync(0xffffffffu, rot, leader);
-      c = __shfl_sync(0xffffffffu, c, leader);
-      sn = __shfl_sync(0xffffffffu, sn, leader);
-      if (valid && rot) {
-        double* mi = M + i * ldm;
-        double* mj = M + j * ldm;
-        for (int r = tl; r < rows; r += ts) {
-          const double u = mi[r], v = mj[r];
-          mi[r] = fma(c, u, -sn * v);
-          mj[r] = fma(sn, u, c * v);
+      __syncthreads();
+      // phase C: apply the rotations (skipped when none in this round)
+      if (nround) {
+        for (int p0 = 0; p0 < npairs; p0 += nteam) {
+          const int p = p0 + team;
+          if (p < npairs && rs[p] != 0.0) {
+            const int i = svd_pair_i(rnd, p, ce), j = svd_pair_j(rnd, p, ce);
+            const double c = rc[p], sn = rs[p];
+            double* mi = M + i * ldm;
+            double* mj = M + j * ldm;
+            for (int r = tl; r < rows; r += ts) {
+              const double u = mi[r], v = mj[r];
+              mi[r] = fma(c, u, -sn * v);
+              mj[r] = fma(sn, u, c * v);
+            }
+          }
         }
+        __syncthreads();
+        if (threadIdx.x == 0) nround = 0;
       }
       __syncthreads();
     }
@@ -637,30 +679,51 @@ __global__ void __launch_bounds__(256) k_norm(const ExecCtx* __restrict__ px, co
       e[n - 2] = G[(n - 1) * ld + (n - 2)];
     }
     d[n - 1] = G[(n - 1) * ld + (n - 1)];
-    // largest eigenvalue of the tridiagonal (d, e) by bisection
+    // Gershgorin interval of the tridiagonal (d, e)
     double lo = d[0], hi = d[0];
     for (int i = 0; i < n; ++i) {
       const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
       lo = fmin(lo, d[i] - r);
       hi = fmax(hi, d[i] + r);
     }
-    const double scale = fmax(fabs(lo), fabs(hi));
-    lo = fmax(lo, 0.0);  // G is positive semi-definite
-    for (int it = 0; it < 200 && hi - lo > 2.0e-16 * scale; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      // Sturm count: number of eigenvalues below mid
-      int cnt = 0;
-      double q = d[0] - mid;
+    for (int i = 0; i + 1 < n; ++i) w[i] = e[i] * e[i];
+    sh[0] = fmax(lo, 0.0);  // G is positive semi-definite
+    sh[1] = hi;
+    sh[2] = fmax(fabs(lo), fabs(hi));
+  }
+  __syncthreads();
+  // largest eigenvalue by multisection: each round every thread takes the
+  // Sturm count (eigenvalues below its point) at one of blockDim.x equally
+  // spaced interior points; the first point with all n below is the new
+  // upper end, the point before it the new lower end.
+  __shared__ int first_all;
+  const double scale = sh[2];
+  for (int it = 0; it < 16; ++it) {
+    const double lo = sh[0], hi = sh[1];
+    if (!(hi - lo > 2.0e-16 * scale)) break;
+    if (threadIdx.x == 0) first_all = blockDim.x;
+    __syncthreads();
+    const double step = (hi - lo) / (double)(blockDim.x + 1);
+    const double pt = fma((double)(threadIdx.x + 1), step, lo);
+    int cnt = 0;
+    double q = d[0] - pt;
+    cnt += q < 0.0;
+    for (int i = 1; i < n; ++i) {
+      if (q == 0.0) q = 1e-300;
+      q = d[i] - pt - w[i - 1] / q;
       cnt += q < 0.0;
-      for (int i = 1; i < n; ++i) {
-        if (q == 0.0) q = 1e-300;
-        q = d[i] - mid - e[i - 1] * e[i - 1] / q;
-        cnt += q < 0.0;
-      }
-      if (cnt == n) hi = mid;
-      else lo = mid;
     }
-    const double s0 = sqrt(fmax(hi, 0.0));
+    if (cnt == n) atomicMin(&first_all, (int)threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int f = first_all;
+      if (f < (int)blockDim.x) sh[1] = fma((double)(f + 1), step, lo);
+      if (f > 0) sh[0] = fma((double)f, step, lo);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double s0 = sqrt(fmax(sh[1], 0.0));
     x.nrm[J.norm_idx] = s0;
     x.scal[J.norm_idx] = s0 > 0.0 ? 1.0 / s0 : 0.0;
   }
@@ -732,7 +795,10 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t
       k_qapply<<<st.count, 256, 0, s>>>(x, j.qapply + st.first);
       break;
     case ST_SVD:
-      k_svd<<<st.count, 256, st.smem > 0 ? (size_t)st.smem : svd_smem, s>>>(x, j.svd + st.first, st.first);
+      {
+      const size_t sm = st.smem > 0 ? (size_t)st.smem : svd_smem;
+      k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first, (int)(sm / 8));
+    }
       break;
     case ST_NORM:
       k_norm<<<st.count, 256, norm_smem_bytes(), s>>>(x, j.norm + st.first);

@@ -206,7 +206,9 @@ struct Builder {
   }
   void flush_svd(int tag) {
     if (sv.empty()) return;
-    const int smem = (int)(sizeof(double) * (size_t)(sv_maxr + 1) * sv_maxc);
+    // shared memory for the largest job, capped at 129 x 64 doubles (66 KB,
+    // three CTAs per SM); larger jobs run in place in global memory
+    const int smem = (int)(sizeof(double) * std::min<size_t>((size_t)(sv_maxr + 1) * sv_maxc, 129 * 64));
     P.stages.push_back(Stage{ST_SVD, (int64_t)P.svd.size(), (int)sv.size(), tag, smem});
     P.svd.insert(P.svd.end(), sv.begin(), sv.end());
     sv.clear();
