@@ -223,11 +223,74 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// Householder on a column-major matrix a (rows x cols, leading dimension lda),
-// one warp per trailing column; `a` is global or shared memory.
-__device__ void householder_cols(double* a, int lda, int rows, int cols, double* tau, double* red, double* sh) {
+constexpr int QR_MAXPIV = 128;  // largest column count of a pivoted QR
+
+// Householder QR on a column-major matrix a (rows x cols, leading dimension
+// lda), in place; `a` is global or shared memory.  With piv != nullptr the
+// columns are pivoted (column of largest remaining norm first, lowest index on
+// ties): cn holds the squared norms of the trailing parts, downdated after each
+// step and recomputed exactly where the downdate has cancelled below 2^-26 of
+// the value at the last recomputation; cn0 holds that value.
+__device__ void householder_cols(double* a, int lda, int rows, int cols, double* tau, double* red, double* sh,
+                                 int* piv, double* cn, double* cn0, int* shp) {
   const int q = min(rows, cols);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  constexpr double kRecompute = 1.4901161193847656e-08;  // 2^-26
+  if (piv) {
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) piv[c] = c;
+    for (int c = warp; c < cols; c += nwarp) {
+      const double* cc = a + (int64_t)c * lda;
+      double s = 0.0;
+      for (int i = lane; i < rows; i += 32) s = fma(cc[i], cc[i], s);
+      s = warp_sum(s);
+      if (lane == 0) cn[c] = cn0[c] = s;
+    }
+    __syncthreads();
+  }
   for (int j = 0; j < q; ++j) {
+    if (piv) {
+      if (warp == 0) {
+        double bv = -1.0;
+        int bi = j;
+        for (int c = j + lane; c < cols; c += 32)
+          if (cn[c] > bv) {
+            bv = cn[c];
+            bi = c;
+          }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+          }
+        }
+        if (lane == 0) *shp = bi;
+      }
+      __syncthreads();
+      const int p = *shp;
+      if (p != j) {
+        double* cj = a + (int64_t)j * lda;
+        double* cp = a + (int64_t)p * lda;
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+          const double t = cj[i];
+          cj[i] = cp[i];
+          cp[i] = t;
+        }
+        if (threadIdx.x == 0) {
+          double t = cn[j];
+          cn[j] = cn[p];
+          cn[p] = t;
+          t = cn0[j];
+          cn0[j] = cn0[p];
+          cn0[p] = t;
+          const int pi = piv[j];
+          piv[j] = piv[p];
+          piv[p] = pi;
+        }
+        __syncthreads();
+      }
+    }
     double* col = a + (int64_t)j * lda;
     double s2 = 0.0;
     for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) s2 = fma(col[i], col[i], s2);
@@ -265,10 +328,37 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
           for (int i = j + 1 + tl; i < rows; i += ts) p = fma(col[i], cc[i], p);
         }
         for (int o = ts >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        const double w = t * (cj + p);
         if (c < cols) {
-          const double w = t * (cj + p);
           if (tl == 0) cc[j] -= w;
           for (int i = j + 1 + tl; i < rows; i += ts) cc[i] = fma(-w, col[i], cc[i]);
+        }
+        if (piv) {
+          // downdate the trailing norm by the new row-j entry; recompute on cancellation
+          const double rj = cj - w;
+          const double nd = c < cols ? cn[c] - rj * rj : 0.0;
+          const bool need = c < cols && nd <= kRecompute * cn0[c];
+          if (__any_sync(0xffffffffu, need)) {
+            double e = 0.0;
+            if (need)
+              for (int i = j + 1 + tl; i < rows; i += ts) e = fma(cc[i], cc[i], e);
+            for (int o = ts >> 1; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if (need && tl == 0) cn[c] = cn0[c] = e;
+          }
+          if (c < cols && !need && tl == 0) cn[c] = nd;
+        }
+      }
+    } else if (piv) {
+      // no reflection: the trailing parts lose row j only
+      for (int c = j + 1 + threadIdx.x; c < cols; c += blockDim.x) {
+        const double* cc = a + (int64_t)c * lda;
+        const double nd = cn[c] - cc[j] * cc[j];
+        if (nd <= kRecompute * cn0[c]) {
+          double e = 0.0;
+          for (int i = j + 1; i < rows; ++i) e = fma(cc[i], cc[i], e);
+          cn[c] = cn0[c] = e;
+        } else {
+          cn[c] = nd;
         }
       }
     }
@@ -284,16 +374,26 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
   extern __shared__ double sm[];
   __shared__ double red[32];
   __shared__ double sh[2];
+  __shared__ double cn[QR_MAXPIV], cn0[QR_MAXPIV];
+  __shared__ int shp;
   const QrJob& J = jobs[blockIdx.x];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
   double* a = ptrv(J.a, x);
   double* tau = ptrv(J.tau, x);
   double* r = ptrv(J.r, x);
+  int* piv = reinterpret_cast<int*>(ptrv(J.piv, x));
+  if (piv && cols > QR_MAXPIV) {
+    // too wide to pivot: unpivoted factorisation, identity order
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) piv[c] = c;
+    piv = nullptr;
+  }
   const int lda = J.lda;
   const int q = min(rows, cols);
   if (rows <= 0 || cols <= 0) {
     if (r)
       for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) r[(int64_t)(e / cols) * J.ldr + e % cols] = 0.0;
+    if (piv)
+      for (int c = threadIdx.x; c < cols; c += blockDim.x) piv[c] = c;
     return;
   }
   if ((int64_t)rows * cols <= smem_doubles) {
@@ -303,7 +403,7 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
       sm[e] = a[(int64_t)c * lda + i];
     }
     __syncthreads();
-    householder_cols(sm, rows, rows, cols, tau, red, sh);
+    householder_cols(sm, rows, rows, cols, tau, red, sh, piv, cn, cn0, &shp);
     if (J.keep)
       for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
         const int c = (int)(e / rows), i = (int)(e % rows);
@@ -317,7 +417,7 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
     return;
   }
   // general case: in place in global memory
-  householder_cols(a, lda, rows, cols, tau, red, sh);
+  householder_cols(a, lda, rows, cols, tau, red, sh, piv, cn, cn0, &shp);
   if (r)
     for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
       const int i = e / cols, c = e % cols;
@@ -561,11 +661,13 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
   if (sig)
     for (int c = threadIdx.x; c < cols; c += blockDim.x) sig[spos[c]] = snorm[c];
   double* U = ptrv(J.u, x);
+  const int* upiv = reinterpret_cast<const int*>(ptrv(J.piv, x));
   if (U) {
     for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
       int r = e / cols, c = e % cols;
       const double s = snorm[c];
-      U[(int64_t)r * J.ldu + spos[c]] = s > 0.0 ? M[c * ldm + r] / s : 0.0;
+      const int ur = upiv ? upiv[r] : r;
+      U[(int64_t)ur * J.ldu + spos[c]] = s > 0.0 ? M[c * ldm + r] / s : 0.0;
     }
   }
   __syncthreads();

@@ -81,6 +81,11 @@ struct QrJob {
   int lda, ldr;
   Dim rows, cols;
   int keep;
+  // Column pivoting (largest remaining column norm first) when piv is set:
+  // a P = Q R with P[:, j] = e_{piv[j]}; piv holds cols int32 (cols <= 128,
+  // else the factorisation is unpivoted and piv the identity).  Used where an
+  // SVD of R^T follows: its one-sided Jacobi then needs about half the sweeps.
+  Ptr piv;
 };
 
 // out(rows x ncols) = H_0 H_1 ... H_{q-1} [Y; 0]  with the reflectors of a QrJob
@@ -112,6 +117,11 @@ struct SvdJob {
   int rank_slot;
   int cap;
   int norm_idx;
+  // Row permutation of U (int32, rows entries, or none): row r of M's left
+  // singular vectors is written to row piv[r] of U.  With M = R^T from a
+  // pivoted QR of A (A P = Q R), this yields the singular vectors for A's
+  // column order.
+  Ptr piv;
 };
 
 // Spectral norm of the square matrix N (n x n, row-major): lambda_max(N^T N)

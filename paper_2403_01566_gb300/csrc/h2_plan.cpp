@@ -167,8 +167,9 @@ struct Builder {
   // QR job; maxr/maxc are the largest values rows/cols can take (shared-memory
   // sizing of the stage); keep = 1 when a Q application needs the reflectors.
   int qr_smem = 0;
-  void qr(Ptr a, int lda, Dim rows, Dim cols, Ptr tau, Ptr r, int ldr, int keep, int maxr, int maxc) {
-    qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep});
+  void qr(Ptr a, int lda, Dim rows, Dim cols, Ptr tau, Ptr r, int ldr, int keep, int maxr, int maxc,
+          Ptr piv = NONE()) {
+    qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep, piv});
     const int64_t cap = 6144;  // doubles, as in the kernel
     int64_t need = (int64_t)maxr * maxc;
     if (need > cap) need = 0;  // this job runs in global memory
@@ -196,7 +197,7 @@ struct Builder {
     if (rows.max > SVD_MAXDIM || cols.max > SVD_MAXDIM) throw std::runtime_error("svd too large");
     svd_size(rows.max, cols.max);
     sv.push_back(SvdJob{src, u, sig, lds, ldu, rows.d(), cols.d(), trans, mode, tol, tol_idx, rank_slot, cap,
-                        norm_idx});
+                        norm_idx, NONE()});
   }
   void svd_size(int rows, int cols) {
     sv_maxr = std::max(sv_maxr, rows);
@@ -958,7 +959,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       }
       const int64_t mark = B.ws;
       struct Scr {
-        int64_t W1, W2, tau1, tau2, rho1, rho2, Gc, Wc, tauc, rhoc, U, sig;
+        int64_t W1, W2, tau1, tau2, rho1, rho2, Gc, Wc, tauc, rhoc, U, sig, piv;
         int qc_max;
       };
       std::vector<Scr> scr(jobs.size());
@@ -997,6 +998,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         s.rhoc = B.alloc((int64_t)(m1 + m2) * AGGC);
         s.U = B.alloc((int64_t)(m1 + m2) * AGGC);
         s.sig = B.alloc(m1 + m2);
+        s.piv = B.alloc((m1 + m2 + 1) / 2);  // int32 pivot order of the condensed QR
         if (m1 + m2 > AGGC) throw std::runtime_error("agglomeration width");
       }
       B.flush_copy(TAG_AGG);
@@ -1054,7 +1056,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         const int rows = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
         const Dim wd = merged_width(J.f1.m, J.f2.m);
         B.qr(PT(AR_WS, s.Wc), rows, DC(rows), wd, PT(AR_WS, s.tauc), PT(AR_WS, s.rhoc), AGGC, 0, rows,
-             J.f1.m.max + J.f2.m.max);
+             J.f1.m.max + J.f2.m.max, PT(AR_WS, s.piv));
       }
       B.flush_qr(TAG_AGG);
       for (size_t j = 0; j < jobs.size(); ++j) {
@@ -1071,7 +1073,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         qcols.mc = gc_rows;
         B.svd_size(m1 + m2, std::min(m1 + m2, gc_rows));
         B.sv.push_back(SvdJob{PT(AR_WS, s.rhoc), PT(AR_WS, s.U), PT(AR_WS, s.sig), AGGC, AGGC, wd, qcols, 1, 2, J.rel,
-                              PARAM_TOL_AGG, outs[j].m.s, AGGM, -1});
+                              PARAM_TOL_AGG, outs[j].m.s, AGGM, -1, PT(AR_WS, s.piv)});
       }
       B.flush_svd(TAG_AGG);
       for (size_t j = 0; j < jobs.size(); ++j) {
@@ -1199,7 +1201,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     std::map<std::pair<int, int>, int64_t> lam;  // Lambda-hat_{c,b} = V_c^* L_b|_c (KP x MB)
     // per level
     std::vector<int> cl, offslot, wmax;
-    std::vector<int64_t> panel, rbuf, ubuf, tbuf;
+    std::vector<int64_t> panel, rbuf, ubuf, tbuf, pbuf;
   };
   auto make_basis_side = [&](bool rowside) {
     Side S;
@@ -1239,6 +1241,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     S.rbuf.assign(T.ncl, -1);
     S.ubuf.assign(T.ncl, -1);
     S.tbuf.assign(T.ncl, -1);
+    S.pbuf.assign(T.ncl, -1);
     for (int c : S.cl) {
       std::vector<int> in;
       for (int b : S.star[c]) {
@@ -1260,6 +1263,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       S.rbuf[c] = B.alloc((int64_t)n * n);
       S.ubuf[c] = B.alloc((int64_t)n * n);
       S.tbuf[c] = B.alloc(n);
+      S.pbuf[c] = B.alloc((n + 1) / 2);  // int32 pivot order of the panel QR
       const int lev = T.level[c];
       for (size_t i = 0; i < S.star[c].size(); ++i) {
         const Final& F = fin[S.star[c][i]];
@@ -1294,7 +1298,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       const int n = T.leaf(c) ? T.size[c] : 2 * KP;
       const int nsl = S.offslot[c] + (int)S.star[c].size();  // total width slot
       B.qr(PT(AR_WS, S.panel[c]), S.wmax[c], DS(nsl), rows_dim(S, c), PT(AR_WS, S.tbuf[c]), PT(AR_WS, S.rbuf[c]), n,
-           0, S.wmax[c], n);
+           0, S.wmax[c], n, PT(AR_WS, S.pbuf[c]));
     }
   };
   // phase 3: Jacobi SVD of R^T with the truncation rule
@@ -1308,7 +1312,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       qcols.mc = 0;
       qcols.ms = S.offslot[c] + (int)S.star[c].size();
       B.sv.push_back(SvdJob{PT(AR_WS, S.rbuf[c]), PT(AR_WS, S.ubuf[c]), NONE(), n, n, rows_d, qcols, 1, 1, tol_mult,
-                            PARAM_TOL_BASIS, S.rank[c], KP, -1});
+                            PARAM_TOL_BASIS, S.rank[c], KP, -1, PT(AR_WS, S.pbuf[c])});
     }
   };
   // phase 4: new basis: leaves V_c = U[:, :k_c]; inner E_{c1}, E_{c2} = blocks of U[:, :k_c]
