@@ -231,8 +231,12 @@ constexpr int QR_MAXPIV = 128;  // largest column count of a pivoted QR
 // ties): cn holds the squared norms of the trailing parts, downdated after each
 // step and recomputed exactly where the downdate has cancelled below 2^-26 of
 // the value at the last recomputation; cn0 holds that value.
-__device__ void householder_cols(double* a, int lda, int rows, int cols, double* tau, double* red, double* sh,
-                                 int* piv, double* cn, double* cn0, int* shp) {
+//
+// Each step: warp 0 alone picks the pivot, swaps, forms the reflector and
+// scales it (no block barrier inside), then all warps update the trailing
+// columns; two block barriers per step.
+__device__ void householder_cols(double* a, int lda, int rows, int cols, double* tau, double* sh, int* piv,
+                                 double* cn, double* cn0) {
   const int q = min(rows, cols);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   constexpr double kRecompute = 1.4901161193847656e-08;  // 2^-26
@@ -248,8 +252,9 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
     __syncthreads();
   }
   for (int j = 0; j < q; ++j) {
-    if (piv) {
-      if (warp == 0) {
+    double* col = a + (int64_t)j * lda;
+    if (warp == 0) {
+      if (piv) {
         double bv = -1.0;
         int bi = j;
         for (int c = j + lane; c < cols; c += 32)
@@ -265,54 +270,48 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
             bi = oi;
           }
         }
-        if (lane == 0) *shp = bi;
-      }
-      __syncthreads();
-      const int p = *shp;
-      if (p != j) {
-        double* cj = a + (int64_t)j * lda;
-        double* cp = a + (int64_t)p * lda;
-        for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-          const double t = cj[i];
-          cj[i] = cp[i];
-          cp[i] = t;
+        if (bi != j) {
+          double* cp = a + (int64_t)bi * lda;
+          for (int i = lane; i < rows; i += 32) {
+            const double t = col[i];
+            col[i] = cp[i];
+            cp[i] = t;
+          }
+          if (lane == 0) {
+            double t = cn[j];
+            cn[j] = cn[bi];
+            cn[bi] = t;
+            t = cn0[j];
+            cn0[j] = cn0[bi];
+            cn0[bi] = t;
+            const int pi = piv[j];
+            piv[j] = piv[bi];
+            piv[bi] = pi;
+          }
+          __syncwarp();
         }
-        if (threadIdx.x == 0) {
-          double t = cn[j];
-          cn[j] = cn[p];
-          cn[p] = t;
-          t = cn0[j];
-          cn0[j] = cn0[p];
-          cn0[p] = t;
-          const int pi = piv[j];
-          piv[j] = piv[p];
-          piv[p] = pi;
-        }
-        __syncthreads();
       }
-    }
-    double* col = a + (int64_t)j * lda;
-    double s2 = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) s2 = fma(col[i], col[i], s2);
-    s2 = block_sum(s2, red);
-    if (threadIdx.x == 0) {
+      double s2 = 0.0;
+      for (int i = j + 1 + lane; i < rows; i += 32) s2 = fma(col[i], col[i], s2);
+      s2 = warp_sum(s2);
       const double alpha = col[j];
       double t = 0.0, sc = 0.0;
       if (s2 > 0.0) {
         const double beta = -copysign(sqrt(alpha * alpha + s2), alpha);
         t = (beta - alpha) / beta;
         sc = 1.0 / (alpha - beta);
-        col[j] = beta;
+        for (int i = j + 1 + lane; i < rows; i += 32) col[i] *= sc;
+        __syncwarp();
+        if (lane == 0) col[j] = beta;
       }
-      sh[0] = t;
-      sh[1] = sc;
-      if (tau) tau[j] = t;
+      if (lane == 0) {
+        sh[0] = t;
+        if (tau) tau[j] = t;
+      }
     }
     __syncthreads();
-    const double t = sh[0], sc = sh[1];
+    const double t = sh[0];
     if (t != 0.0) {
-      for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) col[i] *= sc;
-      __syncthreads();
       // trailing columns: teams of ts lanes per column (short columns use small
       // teams so that the FP64 shuffle reduction stays short)
       const int len = rows - j - 1;
@@ -372,10 +371,8 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
                                             int smem_doubles) {
   const ExecCtx& x = *px;
   extern __shared__ double sm[];
-  __shared__ double red[32];
   __shared__ double sh[2];
   __shared__ double cn[QR_MAXPIV], cn0[QR_MAXPIV];
-  __shared__ int shp;
   const QrJob& J = jobs[blockIdx.x];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
   double* a = ptrv(J.a, x);
@@ -403,7 +400,7 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
       sm[e] = a[(int64_t)c * lda + i];
     }
     __syncthreads();
-    householder_cols(sm, rows, rows, cols, tau, red, sh, piv, cn, cn0, &shp);
+    householder_cols(sm, rows, rows, cols, tau, sh, piv, cn, cn0);
     if (J.keep)
       for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
         const int c = (int)(e / rows), i = (int)(e % rows);
@@ -417,7 +414,7 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
     return;
   }
   // general case: in place in global memory
-  householder_cols(a, lda, rows, cols, tau, red, sh, piv, cn, cn0, &shp);
+  householder_cols(a, lda, rows, cols, tau, sh, piv, cn, cn0);
   if (r)
     for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
       const int i = e / cols, c = e % cols;

@@ -104,9 +104,11 @@ struct Builder {
   std::vector<GemmTerm> gt;
   std::vector<CopyJob> cp;
   std::vector<QrJob> qj;
+  std::vector<double> qj_cost;  // static cost bound of each pending QR job
   std::vector<QApplyJob> qa;
   std::vector<SvdJob> sv;
   int sv_maxr = 1, sv_maxc = 1;  // largest pending SVD job
+  std::vector<double> sv_cost;   // static cost bound of each pending SVD job (from svd_size)
   std::vector<ScanJob> sc;
   std::vector<NormJob> nj;
 
@@ -170,14 +172,30 @@ struct Builder {
   void qr(Ptr a, int lda, Dim rows, Dim cols, Ptr tau, Ptr r, int ldr, int keep, int maxr, int maxc,
           Ptr piv = NONE()) {
     qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep, piv});
+    qj_cost.push_back((double)maxr * maxc * maxc);
     const int64_t cap = 6144;  // doubles, as in the kernel
     int64_t need = (int64_t)maxr * maxc;
     if (need > cap) need = 0;  // this job runs in global memory
     (void)keep;
     qr_smem = (int)std::max<int64_t>(qr_smem, need * 8);
   }
+  // Jobs of one stage are independent: issue them largest first so that the
+  // long ones do not start last and leave the tail of the launch to a few SMs.
+  template <class Job>
+  static void largest_first(std::vector<Job>& jobs, const std::vector<double>& cost) {
+    if (cost.size() != jobs.size()) return;
+    std::vector<int> ord(jobs.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<Job> out;
+    out.reserve(jobs.size());
+    for (int i : ord) out.push_back(jobs[i]);
+    jobs.swap(out);
+  }
   void flush_qr(int tag) {
     if (qj.empty()) return;
+    largest_first(qj, qj_cost);
+    qj_cost.clear();
     P.stages.push_back(Stage{ST_QR, (int64_t)P.qr.size(), (int)qj.size(), tag, qr_smem});
     P.qr.insert(P.qr.end(), qj.begin(), qj.end());
     qj.clear();
@@ -200,6 +218,7 @@ struct Builder {
                         norm_idx, NONE()});
   }
   void svd_size(int rows, int cols) {
+    sv_cost.push_back((double)rows * cols * cols);
     sv_maxr = std::max(sv_maxr, rows);
     sv_maxc = std::max(sv_maxc, cols);
     P.svd_maxrows = std::max(P.svd_maxrows, rows);
@@ -210,6 +229,8 @@ struct Builder {
     // shared memory for the largest job, capped at 129 x 64 doubles (66 KB,
     // three CTAs per SM); larger jobs run in place in global memory
     const int smem = (int)(sizeof(double) * std::min<size_t>((size_t)(sv_maxr + 1) * sv_maxc, 129 * 64));
+    largest_first(sv, sv_cost);
+    sv_cost.clear();
     P.stages.push_back(Stage{ST_SVD, (int64_t)P.svd.size(), (int)sv.size(), tag, smem});
     P.svd.insert(P.svd.end(), sv.begin(), sv.end());
     sv.clear();
