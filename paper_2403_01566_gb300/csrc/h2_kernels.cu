@@ -365,7 +365,72 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
   }
 }
 
-constexpr int QR_SMEM_DOUBLES = 6144;  // 48 KB: in-shared-memory QR up to this size
+// R factor of a tall column-major matrix a (rows x cols) without its Q:
+// row chunks of a stream through shared memory under the triangle accumulated
+// so far, W = [R (cols x cols); chunk (ch x cols)], leading dimension ld.  Each
+// chunk is annihilated column by column by reflectors that touch row j of R
+// and the chunk only (the triangle-on-top step of a tall-skinny QR), so the
+// flop count equals that of Householder QR on a and every load of a is one
+// coalesced pass.  On return W's upper cols x cols triangle holds R.
+__device__ void tsqr_r(const double* __restrict__ a, int lda, int rows, int cols, double* W, int ld, int ch_max,
+                       double* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* C = W + cols;  // chunk rows start below the triangle
+  for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) W[(e / cols) * ld + e % cols] = 0.0;
+  for (int r0 = 0; r0 < rows; r0 += ch_max) {
+    const int ch = min(ch_max, rows - r0);
+    for (int e = threadIdx.x; e < ch * cols; e += blockDim.x) {
+      const int c = e / ch, i = e % ch;
+      C[c * ld + i] = a[(int64_t)c * lda + r0 + i];
+    }
+    __syncthreads();
+    int ts = 32;
+    while (ts > 1 && ts * 8 > ch) ts >>= 1;
+    const int nteam = blockDim.x / ts, team = threadIdx.x / ts, tl = threadIdx.x % ts;
+    for (int j = 0; j < cols; ++j) {
+      double* cj = C + j * ld;
+      if (warp == 0) {
+        double s2 = 0.0;
+        for (int i = lane; i < ch; i += 32) s2 = fma(cj[i], cj[i], s2);
+        s2 = warp_sum(s2);
+        const double alpha = W[j * ld + j];
+        double t = 0.0;
+        if (s2 > 0.0) {
+          const double beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+          t = (beta - alpha) / beta;
+          const double sc = 1.0 / (alpha - beta);
+          for (int i = lane; i < ch; i += 32) cj[i] *= sc;
+          __syncwarp();
+          if (lane == 0) W[j * ld + j] = beta;
+        }
+        if (lane == 0) sh[0] = t;
+      }
+      __syncthreads();
+      const double t = sh[0];
+      if (t != 0.0) {
+        for (int c0 = j + 1; c0 < cols; c0 += nteam) {
+          const int c = c0 + team;
+          double p = 0.0, rjc = 0.0;
+          double* cc = C + c * ld;
+          if (c < cols) {
+            rjc = W[c * ld + j];  // read by every lane before the shuffle (lane 0 writes it below)
+            for (int i = tl; i < ch; i += ts) p = fma(cj[i], cc[i], p);
+          }
+          for (int o = ts >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+          if (c < cols) {
+            const double w = t * (rjc + p);
+            if (tl == 0) W[c * ld + j] = rjc - w;
+            for (int i = tl; i < ch; i += ts) cc[i] = fma(-w, cj[i], cc[i]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+constexpr int QR_TSQR_MAXC = 64;       // widest R-only factorisation that streams row chunks
+constexpr int QR_MAX_SMEM_BYTES = 8 * (QR_TSQR_MAXC + 64) * QR_TSQR_MAXC;  // 64 KB
 
 __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, const QrJob* __restrict__ jobs,
                                             int smem_doubles) {
@@ -410,6 +475,22 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
       for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
         const int i = e / cols, c = e % cols;
         r[(int64_t)i * J.ldr + c] = (c >= i && i < q) ? sm[(int64_t)c * rows + i] : 0.0;
+      }
+    return;
+  }
+  if (!J.keep && cols <= QR_TSQR_MAXC && smem_doubles / cols - cols >= 16) {
+    // R only, tall: stream row chunks through shared memory, then pivot the
+    // (cols x cols) triangle; the reflectors are not kept (no Q application
+    // follows an R-only job)
+    const int ld = smem_doubles / cols;
+    tsqr_r(a, lda, rows, cols, sm, ld, ld - cols, sh);
+    if (piv) householder_cols(sm, ld, cols, cols, nullptr, sh, piv, cn, cn0);
+    if (tau)
+      for (int c = threadIdx.x; c < q; c += blockDim.x) tau[c] = 0.0;
+    if (r)
+      for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
+        const int i = e / cols, c = e % cols;
+        r[(int64_t)i * J.ldr + c] = (c >= i && i < q) ? sm[(int64_t)c * ld + i] : 0.0;
       }
     return;
   }
@@ -458,11 +539,21 @@ __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, 
 // One-sided (Hestenes) Jacobi: rotate pairs of columns of M until all pairs are
 // orthogonal to relative precision; the column norms are the singular values
 // and the normalised columns the left singular vectors.  Pairs follow the
-// round-robin (circle) ordering so that cols/2 disjoint pairs rotate at once,
-// each by a team of lanes.  Squared column norms are kept in shared memory,
-// updated after each rotation (alpha' = alpha - t*gamma, beta' = beta + t*gamma)
-// and recomputed exactly at the start of every sweep, so a pair costs one dot
-// product plus the rotation.
+// round-robin (circle) ordering so that cols/2 disjoint pairs rotate at once.
+// Squared column norms are kept in shared memory, updated after each rotation
+// (alpha' = alpha - t*gamma, beta' = beta + t*gamma) and recomputed exactly at
+// the start of every sweep.
+//
+// The FP64 pipe issues a warp instruction at the same cost however many lanes
+// it uses, so the rounds are laid out to issue few of them:
+//  - dot products: one lane per pair, the warps splitting the rows; the
+//    partial sums meet in shared memory (no shuffle-add chains);
+//  - rotations in scaled form: M = Mt diag(d), and the rotation by
+//    (c, s = c t) of columns i, j becomes Mt_i -= (t d_j/d_i) Mt_j,
+//    Mt_j += (t d_i/d_j) Mt_i (one FMA per element), d_i, d_j *= c; the
+//    scales are folded back into M at the start of every sweep, so Mt grows
+//    by at most 2^(cols/2) within a sweep (|t| <= 1);
+//  - only the pairs that rotate are visited, from a compacted list.
 constexpr int SVD_MAXSWEEP = 60;
 
 // Round-robin (circle method) pairing of ce (even) columns: in round rnd, pair
@@ -486,7 +577,10 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
   __shared__ int nrot;
   __shared__ int nround;
   __shared__ double nrm2[SVD_MAXDIM];
-  __shared__ double gam[SVD_MAXDIM / 2 + 1], rc[SVD_MAXDIM / 2 + 1], rs[SVD_MAXDIM / 2 + 1];
+  __shared__ double dsc[SVD_MAXDIM], dinv[SVD_MAXDIM];  // column scales d and 1/d of M = Mt diag(d)
+  __shared__ double part[256];                          // partial dot products (blockDim <= 256)
+  __shared__ int rlist[SVD_MAXDIM / 2];                 // rotating pairs of the round: (i << 8) | j
+  __shared__ double rfa[SVD_MAXDIM / 2], rfb[SVD_MAXDIM / 2];
   __shared__ double snorm[SVD_MAXDIM];
   __shared__ int spos[SVD_MAXDIM];
   __shared__ double s_fro;
@@ -522,19 +616,34 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
       int r = e / cols, c = e % cols;
       M[c * ldm + r] = J.trans ? S[(int64_t)c * J.lds + r] : S[(int64_t)r * J.lds + c];
     }
-  if (threadIdx.x == 0) {
-    nrot = 0;
-    nround = 0;
+  if (threadIdx.x == 0) nrot = 0;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    dsc[c] = 1.0;
+    dinv[c] = 1.0;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  // exact squared column norms (one warp per column)
+  // fold the scales into M, then exact squared column norms (one warp per column)
   auto col_norms = [&]() {
     for (int c = warp; c < cols; c += nwarp) {
+      const double dc = dsc[c];
+      double* mc = M + c * ldm;
       double p = 0.0;
-      for (int r = lane; r < rows; r += 32) p = fma(M[c * ldm + r], M[c * ldm + r], p);
+      if (dc != 1.0) {
+        for (int r = lane; r < rows; r += 32) {
+          const double v = mc[r] * dc;
+          mc[r] = v;
+          p = fma(v, v, p);
+        }
+      } else {
+        for (int r = lane; r < rows; r += 32) p = fma(mc[r], mc[r], p);
+      }
       p = warp_sum(p);
-      if (lane == 0) nrm2[c] = p;
+      if (lane == 0) {
+        nrm2[c] = p;
+        dsc[c] = 1.0;
+        dinv[c] = 1.0;
+      }
     }
     __syncthreads();
   };
@@ -550,83 +659,73 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
   const int ce = cols + (cols & 1);
   const int npairs = ce / 2;
   const double tol = 2.5e-15;
-  // teams of ts lanes per pair: at least 8 rows per lane, at most a warp
-  int ts = 32;
-  while (ts > 1 && ts * 8 > rows) ts >>= 1;
-  const int nteam = blockDim.x / ts, team = threadIdx.x / ts, tl = threadIdx.x % ts;
+  // dot products: thread -> (pair, row segment)
+  const int nseg = blockDim.x / npairs;
+  const int ap = threadIdx.x % npairs, aseg = threadIdx.x / npairs;
   int sweep = 0;
   for (; sweep < SVD_MAXSWEEP; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int rnd = 0; rnd < ce - 1; ++rnd) {
-      // phase A: dot products gamma_p = m_i . m_j of the round's pairs
-      for (int p0 = 0; p0 < npairs; p0 += nteam) {
-        const int p = p0 + team;
-        double ga = 0.0, g2 = 0.0;
-        if (p < npairs) {
-          const int i = svd_pair_i(rnd, p, ce), j = svd_pair_j(rnd, p, ce);
-          if (j < cols) {
-            const double* mi = M + i * ldm;
-            const double* mj = M + j * ldm;
-            int r = tl;
-            for (; r + ts < rows; r += 2 * ts) {
-              ga = fma(mi[r], mj[r], ga);
-              g2 = fma(mi[r + ts], mj[r + ts], g2);
-            }
-            if (r < rows) ga = fma(mi[r], mj[r], ga);
-          }
-        }
-        ga += g2;
-        for (int o = ts >> 1; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        if (p < npairs && tl == 0) gam[p] = ga;
-      }
-      __syncthreads();
-      // phase B: rotation parameters, one lane per pair (the FP64 divide and
-      // square-root sequences run 32 pairs wide)
-      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-        const int i = svd_pair_i(rnd, p, ce), j = svd_pair_j(rnd, p, ce);
-        double c = 1.0, sn = 0.0;
-        int rot = 0;
+      // phase A: partial dot products of the round's pairs
+      if (aseg < nseg) {
+        const int i = svd_pair_i(rnd, ap, ce), j = svd_pair_j(rnd, ap, ce);
+        double g = 0.0;
         if (j < cols) {
-          const double ga = gam[p], al = nrm2[i], be = nrm2[j];
+          const double* mi = M + i * ldm;
+          const double* mj = M + j * ldm;
+          for (int r = aseg; r < rows; r += nseg) g = fma(mi[r], mj[r], g);
+        }
+        part[aseg * npairs + ap] = g;
+      }
+      if (threadIdx.x == 0) nround = 0;
+      __syncthreads();
+      // phase B: one thread per pair sums the partials and sets up the rotation
+      if (threadIdx.x < npairs) {
+        const int p = threadIdx.x;
+        const int i = svd_pair_i(rnd, p, ce), j = svd_pair_j(rnd, p, ce);
+        if (j < cols) {
+          double gt = part[p];
+          for (int sg = 1; sg < nseg; ++sg) gt += part[sg * npairs + p];
+          const double di = dsc[i], dj = dsc[j];
+          const double ga = gt * di * dj, al = nrm2[i], be = nrm2[j];
           // |ga| > tol * sqrt(al * be), in squared form
           if (ga != 0.0 && al > tiny2 && be > tiny2 && ga * ga > (tol * tol) * al * be) {
             const double zeta = (be - al) / (2.0 * ga);
             const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = rsqrt(1.0 + t * t);
-            sn = c * t;
-            rot = 1;
+            const double q = 1.0 + t * t;
+            const double c = rsqrt(q);
+            const double ei = dinv[i], ej = dinv[j];
             nrm2[i] = fmax(al - t * ga, 0.0);
             nrm2[j] = be + t * ga;
+            dsc[i] = di * c;
+            dsc[j] = dj * c;
+            dinv[i] = ei * (q * c);
+            dinv[j] = ej * (q * c);
+            const int slot = atomicAdd(&nround, 1);
+            rlist[slot] = (i << 8) | j;
+            rfa[slot] = t * dj * ei;
+            rfb[slot] = t * di * ej;
           }
-        }
-        rc[p] = c;
-        rs[p] = rot ? sn : 0.0;
-        if (rot) {
-          rotated = 1;
-          nround = 1;
-          atomicAdd(&nrot, 1);
         }
       }
       __syncthreads();
-      // phase C: apply the rotations (skipped when none in this round)
-      if (nround) {
-        for (int p0 = 0; p0 < npairs; p0 += nteam) {
-          const int p = p0 + team;
-          if (p < npairs && rs[p] != 0.0) {
-            const int i = svd_pair_i(rnd, p, ce), j = svd_pair_j(rnd, p, ce);
-            const double c = rc[p], sn = rs[p];
-            double* mi = M + i * ldm;
-            double* mj = M + j * ldm;
-            for (int r = tl; r < rows; r += ts) {
-              const double u = mi[r], v = mj[r];
-              mi[r] = fma(c, u, -sn * v);
-              mj[r] = fma(sn, u, c * v);
-            }
-          }
+      // phase C: scaled rotations of the pairs that rotate
+      const int nr = nround;
+      if (nr > 0) {
+        for (int e = threadIdx.x; e < nr * rows; e += blockDim.x) {
+          const int sl = e % nr, r = e / nr;
+          const int ij = rlist[sl];
+          double* mi = M + (ij >> 8) * ldm;
+          double* mj = M + (ij & 255) * ldm;
+          const double u = mi[r], v = mj[r];
+          mi[r] = fma(-rfa[sl], v, u);
+          mj[r] = fma(rfb[sl], u, v);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) nround = 0;
+        if (threadIdx.x == 0) {
+          rotated = 1;
+          nrot += nr;
+        }
       }
       __syncthreads();
     }
@@ -865,7 +964,7 @@ cudaError_t kernels_init() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * QR_SMEM_DOUBLES);
+  e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_MAX_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)svd_smem_bytes(SVD_MAXDIM, SVD_MAXDIM));

@@ -175,8 +175,11 @@ struct Builder {
     qj_cost.push_back((double)maxr * maxc * maxc);
     const int64_t cap = 6144;  // doubles, as in the kernel
     int64_t need = (int64_t)maxr * maxc;
-    if (need > cap) need = 0;  // this job runs in global memory
-    (void)keep;
+    if (need > cap) {
+      // R-only jobs up to 64 columns stream 64-row chunks under the triangle;
+      // others run in global memory
+      need = (!keep && maxc <= 64) ? (int64_t)(maxc + 64) * maxc : 0;
+    }
     qr_smem = (int)std::max<int64_t>(qr_smem, need * 8);
   }
   // Jobs of one stage are independent: issue them largest first so that the
