@@ -50,9 +50,10 @@ __device__ __forceinline__ double ld_op(const double* p, int ld, int t, int i, i
 }
 
 // acc[q] += op(A)(m x k) op(B)(k x n) for the outputs of this thread
-__device__ __forceinline__ void gemm_accumulate(double (&acc)[GQ], int nq, int m, int n, int k, const double* A,
+template <int Q>
+__device__ __forceinline__ void gemm_accumulate(double (&acc)[Q], int nq, int m, int n, int k, const double* A,
                                                 int lda, int ta, const double* B, int ldb, int tb, double* As,
-                                                double* Bs) {
+                                                double* Bs, int ldbs) {
   for (int kk = 0; kk < k; kk += GK) {
     const int kc = min(GK, k - kk);
     for (int e = threadIdx.x; e < m * kc; e += 256) {
@@ -61,17 +62,17 @@ __device__ __forceinline__ void gemm_accumulate(double (&acc)[GQ], int nq, int m
     }
     for (int e = threadIdx.x; e < kc * n; e += 256) {
       const int l = e / n, c = e % n;
-      Bs[l * (GT + 1) + c] = ld_op(B, ldb, tb, kk + l, c);
+      Bs[l * ldbs + c] = ld_op(B, ldb, tb, kk + l, c);
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < GQ; ++q) {
+    for (int q = 0; q < Q; ++q) {
       if (q < nq) {
         const int e = threadIdx.x + 256 * q;
         if (e < m * n) {
           const int r = e / n, c = e % n;
           double a = acc[q];
-          for (int l = 0; l < kc; ++l) a = fma(As[r * (GK + 1) + l], Bs[l * (GT + 1) + c], a);
+          for (int l = 0; l < kc; ++l) a = fma(As[r * (GK + 1) + l], Bs[l * ldbs + c], a);
           acc[q] = a;
         }
       }
@@ -80,25 +81,37 @@ __device__ __forceinline__ void gemm_accumulate(double (&acc)[GQ], int nq, int m
   }
 }
 
+// Shared memory of a stage whose outputs are at most mmax rows and whose
+// right factors (and inner widths of three-factor terms) at most nb columns:
+// As mmax x (GK+1), Bs GK x (nb+1), Ts mmax x (nb+1).  Stages of small
+// static shapes thus keep many CTAs resident per SM.
+__host__ __device__ constexpr int gemm_smem_doubles(int mmax, int nb) {
+  return mmax * (GK + 1) + (GK + mmax) * (nb + 1);
+}
+
+// Q = outputs per thread (m * n <= 256 Q): small stages take a small Q, so
+// fewer registers and more resident CTAs per SM.
+template <int Q>
 __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs,
-                                              const GemmTerm* __restrict__ terms) {
+                                              const GemmTerm* __restrict__ terms, int mmax, int nb) {
   const ExecCtx& x = *px;
   extern __shared__ double sm[];
-  double* As = sm;                      // GT x (GK+1)
-  double* Bs = As + GT * (GK + 1);      // GK x (GT+1)
-  double* Ts = Bs + GK * (GT + 1);      // GT x (GT+1)
+  const int ldbs = nb + 1;
+  double* As = sm;                      // mmax x (GK+1)
+  double* Bs = As + mmax * (GK + 1);    // GK x (nb+1)
+  double* Ts = Bs + GK * ldbs;          // mmax x (nb+1)
   const GemmOut& O = outs[blockIdx.x];
   const int m = dimv(O.m, x.slot);
   const int n = O.clampn ? min(dimv(O.n, x.slot), GT) : dimv(O.n, x.slot);
   if (m <= 0 || n <= 0) return;
-  if (m > GT || n > GT) {
+  if (m > mmax || n > nb || m * n > 256 * Q) {
     if (threadIdx.x == 0) set_err(x, -9);
     return;
   }
   const int nq = (m * n + 255) / 256;
-  double acc[GQ];
+  double acc[Q];
 #pragma unroll
-  for (int q = 0; q < GQ; ++q) acc[q] = 0.0;
+  for (int q = 0; q < Q; ++q) acc[q] = 0.0;
 
   for (int ti = O.t0; ti < O.t1; ++ti) {
     const GemmTerm& T = terms[ti];
@@ -109,7 +122,7 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     const double* C = ptrv(T.c, x);
     if (B == nullptr) {  // plain add of op(A) (m x n)
 #pragma unroll
-      for (int q = 0; q < GQ; ++q) {
+      for (int q = 0; q < Q; ++q) {
         const int e = threadIdx.x + 256 * q;
         if (q < nq && e < m * n) acc[q] += alpha * ld_op(A, T.lda, T.ta, e / n, e % n);
       }
@@ -117,49 +130,49 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     }
     const int k1 = dimv(T.k1, x.slot);
     if (C == nullptr) {
-      double tacc[GQ];
+      double tacc[Q];
 #pragma unroll
-      for (int q = 0; q < GQ; ++q) tacc[q] = 0.0;
-      gemm_accumulate(tacc, nq, m, n, k1, A, T.lda, T.ta, B, T.ldb, T.tb, As, Bs);
+      for (int q = 0; q < Q; ++q) tacc[q] = 0.0;
+      gemm_accumulate(tacc, nq, m, n, k1, A, T.lda, T.ta, B, T.ldb, T.tb, As, Bs, ldbs);
 #pragma unroll
-      for (int q = 0; q < GQ; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
+      for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
       continue;
     }
     // three-factor term: Ts = op(A)op(B) (m x nn), then acc += alpha * Ts op(C)
     const int nn = dimv(T.k2, x.slot);
-    if (nn > GT) {
+    if (nn > nb || m * nn > 256 * Q) {
       if (threadIdx.x == 0) set_err(x, -9);
       return;
     }
     const int nq2 = (m * nn + 255) / 256;
-    double tacc[GQ];
+    double tacc[Q];
 #pragma unroll
-    for (int q = 0; q < GQ; ++q) tacc[q] = 0.0;
-    gemm_accumulate(tacc, nq2, m, nn, k1, A, T.lda, T.ta, B, T.ldb, T.tb, As, Bs);
+    for (int q = 0; q < Q; ++q) tacc[q] = 0.0;
+    gemm_accumulate(tacc, nq2, m, nn, k1, A, T.lda, T.ta, B, T.ldb, T.tb, As, Bs, ldbs);
 #pragma unroll
-    for (int q = 0; q < GQ; ++q) {
+    for (int q = 0; q < Q; ++q) {
       const int e = threadIdx.x + 256 * q;
-      if (q < nq2 && e < m * nn) Ts[(e / nn) * (GT + 1) + e % nn] = tacc[q];
+      if (q < nq2 && e < m * nn) Ts[(e / nn) * ldbs + e % nn] = tacc[q];
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < GQ; ++q) tacc[q] = 0.0;
+    for (int q = 0; q < Q; ++q) tacc[q] = 0.0;
     // Ts (m x nn) times op(C) (nn x n); Ts plays the role of A (already in smem)
     for (int kk = 0; kk < nn; kk += GK) {
       const int kc = min(GK, nn - kk);
       for (int e = threadIdx.x; e < kc * n; e += 256) {
         const int l = e / n, c = e % n;
-        Bs[l * (GT + 1) + c] = ld_op(C, T.ldc, T.tc, kk + l, c);
+        Bs[l * ldbs + c] = ld_op(C, T.ldc, T.tc, kk + l, c);
       }
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < GQ; ++q) {
+      for (int q = 0; q < Q; ++q) {
         if (q < nq) {
           const int e = threadIdx.x + 256 * q;
           if (e < m * n) {
             const int r = e / n, c = e % n;
             double a = tacc[q];
-            for (int l = 0; l < kc; ++l) a = fma(Ts[r * (GT + 1) + kk + l], Bs[l * (GT + 1) + c], a);
+            for (int l = 0; l < kc; ++l) a = fma(Ts[r * ldbs + kk + l], Bs[l * ldbs + c], a);
             tacc[q] = a;
           }
         }
@@ -167,11 +180,11 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < GQ; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
+    for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
   }
   double* out = ptrv(O.o, x);
 #pragma unroll
-  for (int q = 0; q < GQ; ++q) {
+  for (int q = 0; q < Q; ++q) {
     const int e = threadIdx.x + 256 * q;
     if (q < nq && e < m * n) {
       double* p = out + (int64_t)(e / n) * O.ldo + e % n;
@@ -503,8 +516,14 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
     }
 }
 
+// out = H_0 ... H_{q-1} [Y; 0].  Threads: column c = tid % nc of out, row
+// segment tid / nc (rows strided by the segment count); per reflector the
+// partial dot products meet in shared memory and one thread per column sums
+// them, so no FP64 shuffle reductions are issued.
 __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, const QApplyJob* __restrict__ jobs) {
   const ExecCtx& x = *px;
+  __shared__ double part[256];
+  __shared__ double wsh[256];
   const QApplyJob& J = jobs[blockIdx.x];
   const int rows = dimv(J.rows, x.slot), q = dimv(J.q, x.slot), nc = dimv(J.ncols, x.slot);
   const double* a = ptrv(J.a, x);
@@ -512,24 +531,39 @@ __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, 
   const double* y = ptrv(J.y, x);
   double* out = ptrv(J.out, x);
   const int ldo = J.ldo;
+  if (nc > (int)blockDim.x) {
+    if (threadIdx.x == 0) set_err(x, -9);
+    return;
+  }
   for (int64_t e = threadIdx.x; e < (int64_t)rows * nc; e += blockDim.x) {
     int i = (int)(e / nc), c = (int)(e % nc);
     out[(int64_t)i * ldo + c] = (i < q) ? y[(int64_t)i * J.ldy + c] : 0.0;
   }
+  if (nc <= 0) return;
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nseg = blockDim.x / nc;
+  const int c = threadIdx.x % nc, sg = threadIdx.x / nc;
+  const bool active = sg < nseg;
   for (int j = min(q, rows) - 1; j >= 0; --j) {
     const double t = tau[j];
-    if (t != 0.0) {
-      const double* v = a + (int64_t)j * J.lda;
-      for (int c = warp; c < nc; c += nw) {
-        double p = 0.0;
-        for (int i = j + 1 + lane; i < rows; i += 32) p += v[i] * out[(int64_t)i * ldo + c];
-        p = warp_sum(p);
-        const double w = t * (out[(int64_t)j * ldo + c] + p);
-        if (lane == 0) out[(int64_t)j * ldo + c] -= w;
-        for (int i = j + 1 + lane; i < rows; i += 32) out[(int64_t)i * ldo + c] -= w * v[i];
-      }
+    if (t == 0.0) continue;
+    const double* v = a + (int64_t)j * J.lda;
+    if (active) {
+      double p = sg == 0 ? out[(int64_t)j * ldo + c] : 0.0;
+      for (int i = j + 1 + sg; i < rows; i += nseg) p = fma(v[i], out[(int64_t)i * ldo + c], p);
+      part[sg * nc + c] = p;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nc) {
+      double sum = part[threadIdx.x];
+      for (int g = 1; g < nseg; ++g) sum += part[g * nc + threadIdx.x];
+      wsh[threadIdx.x] = t * sum;
+    }
+    __syncthreads();
+    if (active) {
+      const double w = wsh[c];
+      if (sg == 0) out[(int64_t)j * ldo + c] -= w;
+      for (int i = j + 1 + sg; i < rows; i += nseg) out[(int64_t)i * ldo + c] = fma(-w, v[i], out[(int64_t)i * ldo + c]);
     }
     __syncthreads();
   }
@@ -885,41 +919,44 @@ __global__ void __launch_bounds__(256) k_norm(const ExecCtx* __restrict__ px, co
       hi = fmax(hi, d[i] + r);
     }
     for (int i = 0; i + 1 < n; ++i) w[i] = e[i] * e[i];
-    sh[0] = fmax(lo, 0.0);  // G is positive semi-definite
+    double dmax = d[0];
+    for (int i = 1; i < n; ++i) dmax = fmax(dmax, d[i]);
+    sh[0] = fmax(fmax(lo, dmax), 0.0);  // lambda_max >= every diagonal entry; G is semi-definite
     sh[1] = hi;
     sh[2] = fmax(fabs(lo), fabs(hi));
   }
   __syncthreads();
-  // largest eigenvalue by multisection: each round every thread takes the
-  // Sturm count (eigenvalues below its point) at one of blockDim.x equally
-  // spaced interior points; the first point with all n below is the new
-  // upper end, the point before it the new lower end.
-  __shared__ int first_all;
-  const double scale = sh[2];
-  for (int it = 0; it < 16; ++it) {
-    const double lo = sh[0], hi = sh[1];
-    if (!(hi - lo > 2.0e-16 * scale)) break;
-    if (threadIdx.x == 0) first_all = blockDim.x;
-    __syncthreads();
-    const double step = (hi - lo) / (double)(blockDim.x + 1);
-    const double pt = fma((double)(threadIdx.x + 1), step, lo);
-    int cnt = 0;
-    double q = d[0] - pt;
-    cnt += q < 0.0;
-    for (int i = 1; i < n; ++i) {
-      if (q == 0.0) q = 1e-300;
-      q = d[i] - pt - w[i - 1] / q;
+  // largest eigenvalue by multisection on one warp: each round every lane takes
+  // the Sturm count (eigenvalues below its point) at one of 32 equally spaced
+  // interior points; the first point with all n below is the new upper end,
+  // the point before it the new lower end.  (A warp instruction costs the same
+  // however many lanes it uses, so one warp of points beats both single-lane
+  // bisection and a block of points.)
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double lo = sh[0], hi = sh[1];
+    const double scale = sh[2];
+    for (int it = 0; it < 24 && hi - lo > 2.0e-16 * scale; ++it) {
+      const double step = (hi - lo) / 33.0;
+      const double pt = fma((double)(lane + 1), step, lo);
+      int cnt = 0;
+      double q = d[0] - pt;
       cnt += q < 0.0;
+      for (int i = 1; i < n; ++i) {
+        if (q == 0.0) q = 1e-300;
+        q = d[i] - pt - w[i - 1] / q;
+        cnt += q < 0.0;
+      }
+      const unsigned all = __ballot_sync(0xffffffffu, cnt == n);
+      const int f = all ? __ffs(all) - 1 : 32;  // first point with every eigenvalue below
+      const double nlo = f > 0 ? fma((double)f, step, lo) : lo;
+      const double nhi = f < 32 ? fma((double)(f + 1), step, lo) : hi;
+      lo = nlo;
+      hi = nhi;
     }
-    if (cnt == n) atomicMin(&first_all, (int)threadIdx.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int f = first_all;
-      if (f < (int)blockDim.x) sh[1] = fma((double)(f + 1), step, lo);
-      if (f > 0) sh[0] = fma((double)f, step, lo);
-    }
-    __syncthreads();
+    if (lane == 0) sh[1] = hi;
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const double s0 = sqrt(fmax(sh[1], 0.0));
     x.nrm[J.norm_idx] = s0;
@@ -953,14 +990,18 @@ __global__ void k_finalize(const ExecCtx* __restrict__ px) {
 
 // ------------------------------------------------------------- launchers ----
 size_t norm_smem_bytes() { return sizeof(double) * 2 * GT * (GT + 1); }
-size_t gemm_smem_bytes() { return sizeof(double) * (GT * (GK + 1) + GK * (GT + 1) + GT * (GT + 1)); }
+size_t gemm_smem_bytes() { return sizeof(double) * gemm_smem_doubles(GT, GT); }
 size_t svd_smem_bytes(int rows, int cols) { return sizeof(double) * (size_t)(rows + 1) * cols; }
 
 static bool g_attr_done = false;
 
 cudaError_t kernels_init() {
   if (g_attr_done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(k_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm<GQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes());
   if (e != cudaSuccess) return e;
@@ -981,7 +1022,17 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t
   if (st.count <= 0) return;
   switch (st.kind) {
     case ST_GEMM:
-      k_gemm<<<st.count, 256, gemm_smem_bytes(), s>>>(x, j.gemm_out + st.first, j.gemm_term);
+    {
+      const int mmax = st.aux ? (st.aux >> 16) : GT, nb = st.aux ? (st.aux & 0xffff) : GT;
+      const size_t sm = sizeof(double) * gemm_smem_doubles(mmax, nb);
+      const int cells = mmax * nb;
+      if (cells <= 256)
+        k_gemm<1><<<st.count, 256, sm, s>>>(x, j.gemm_out + st.first, j.gemm_term, mmax, nb);
+      else if (cells <= 1024)
+        k_gemm<4><<<st.count, 256, sm, s>>>(x, j.gemm_out + st.first, j.gemm_term, mmax, nb);
+      else
+        k_gemm<GQ><<<st.count, 256, sm, s>>>(x, j.gemm_out + st.first, j.gemm_term, mmax, nb);
+    }
       break;
     case ST_COPY:
       k_copy<<<st.count, 256, 0, s>>>(x, j.copy + st.first);

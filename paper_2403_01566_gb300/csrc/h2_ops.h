@@ -152,6 +152,7 @@ struct Stage {
   int count;      // number of jobs
   int tag;        // phase id, for profiling
   int smem;       // dynamic shared memory of the launch (SVD stages: largest job)
+  int aux;        // GEMM stages: (largest m << 16) | largest n or inner width (0: 64, 64)
 };
 
 // Kernel parameters common to all stages.

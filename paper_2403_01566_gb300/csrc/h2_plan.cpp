@@ -126,8 +126,16 @@ struct Builder {
   int scal() { return P.nscal++; }
 
   // ---- GEMM jobs
+  // Static upper bound of a dim (slot-valued dims: the 64-wide tile limit).
+  static int dim_bound(const Dim& d) {
+    if (d.s1 >= 0 || d.s2 >= 0) return d.mc >= 0 && d.ms < 0 ? std::min(d.mc, 64) : 64;
+    return std::min(d.mc >= 0 && d.ms < 0 ? std::min(d.c, d.mc) : d.c, 64);
+  }
+  int g_mmax = 1, g_nb = 1;  // shape bounds of the pending GEMM stage
   void out(Ptr o, int ldo, Dim m, Dim n, int beta, int clampn = 0) {
     go.push_back(GemmOut{o, ldo, m, n, beta, (int)gt.size(), (int)gt.size(), clampn});
+    g_mmax = std::max(g_mmax, dim_bound(m));
+    g_nb = std::max(g_nb, clampn ? 64 : dim_bound(n));
   }
   void term2(MRef a, MRef b, Dim k1, double alpha = 1.0, int sidx = -1) {
     gt.push_back(GemmTerm{a.p, b.p, NONE(), a.ld, b.ld, 0, k1, DC(0), a.t, b.t, 0, alpha, sidx});
@@ -136,6 +144,7 @@ struct Builder {
   void term3(MRef a, MRef b, MRef c, Dim k1, Dim k2, double alpha = 1.0) {
     gt.push_back(GemmTerm{a.p, b.p, c.p, a.ld, b.ld, c.ld, k1, k2, a.t, b.t, c.t, alpha, -1});
     go.back().t1++;
+    g_nb = std::max(g_nb, dim_bound(k2));
   }
   void add(MRef a, double alpha = 1.0) {
     gt.push_back(GemmTerm{a.p, NONE(), NONE(), a.ld, 0, 0, DC(0), DC(0), a.t, 0, 0, alpha, -1});
@@ -151,9 +160,10 @@ struct Builder {
       P.gout.push_back(o);
     }
     P.gterm.insert(P.gterm.end(), gt.begin(), gt.end());
-    P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag, 0});
+    P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag, 0, (g_mmax << 16) | g_nb});
     go.clear();
     gt.clear();
+    g_mmax = g_nb = 1;
   }
   // ---- copies
   void copy(Ptr src, int lds, Ptr dst, int ldd, Dim rows, Dim cols, int trans, double alpha = 1.0,
@@ -173,15 +183,16 @@ struct Builder {
           Ptr piv = NONE()) {
     qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep, piv});
     qj_cost.push_back((double)maxr * maxc * maxc);
-    const int64_t cap = 6144;  // doubles, as in the kernel
-    int64_t need = (int64_t)maxr * maxc;
-    if (need > cap) {
-      // R-only jobs up to 64 columns stream 64-row chunks under the triangle;
-      // others run in global memory
-      need = (!keep && maxc <= 64) ? (int64_t)(maxc + 64) * maxc : 0;
+    const int64_t cap = 6144;  // doubles (48 KB)
+    const int64_t need = (int64_t)maxr * maxc;
+    if (need <= cap) {
+      qr_smem = (int)std::max<int64_t>(qr_smem, need * 8);
+    } else if (!keep && maxc <= 64) {
+      // R-only: may stream 64-row chunks under the triangle
+      qr_tsqr = (int)std::max<int64_t>(qr_tsqr, (int64_t)(maxc + 64) * maxc * 8);
     }
-    qr_smem = (int)std::max<int64_t>(qr_smem, need * 8);
   }
+  int qr_tsqr = 0;
   // Jobs of one stage are independent: issue them largest first so that the
   // long ones do not start last and leave the tail of the launch to a few SMs.
   template <class Job>
@@ -199,10 +210,16 @@ struct Builder {
     if (qj.empty()) return;
     largest_first(qj, qj_cost);
     qj_cost.clear();
-    P.stages.push_back(Stage{ST_QR, (int64_t)P.qr.size(), (int)qj.size(), tag, qr_smem});
+    // Streaming row chunks trades L2 traffic for more, shorter steps: a win
+    // when many jobs keep every SM busy, a loss for a few latency-bound ones,
+    // which then run in global memory.
+    int smem = qr_smem;
+    if (qj.size() >= 2048) smem = std::max(smem, qr_tsqr);
+    P.stages.push_back(Stage{ST_QR, (int64_t)P.qr.size(), (int)qj.size(), tag, smem});
     P.qr.insert(P.qr.end(), qj.begin(), qj.end());
     qj.clear();
     qr_smem = 0;
+    qr_tsqr = 0;
   }
   void qapply(Ptr a, int lda, Ptr tau, Dim rows, Dim q, Ptr y, int ldy, Dim ncols, Ptr outp, int ldo) {
     qa.push_back(QApplyJob{a, tau, y, outp, lda, ldy, ldo, rows, q, ncols});
