@@ -257,11 +257,16 @@ def main():
     dom_name, dom = max(kinds, key=lambda kv: kv[1].ms)
     peak = fp64_peak()
     achieved = dom.flops / (dom.ms / 1e3) / 1e12 if dom.ms > 0 else 0.0
+    # DRAM bytes per launch from the committed ncu capture, valid only while the
+    # kernel source is the one the counters were taken on
     traffic = None
     try:
+        import hashlib
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        traffic = tr.get(dom_name)
-    except Exception:
+        src = os.path.join(ROOT, "paper_2403_01566_gb300", "csrc", "h2_kernels.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("kernels_source_sha256"):
+            traffic = tr["per_launch_bytes"].get(dom_name)
+    except (OSError, ValueError, KeyError):
         pass
 
     cpu = None
@@ -287,6 +292,8 @@ def main():
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
+                         "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                         "launches": dom.launches, "flop_per_launch": dom.flops / dom.launches if dom.launches else None,
                          "peak_source": "FP64 ALU peak derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
                          "share": dom.ms / prof_total if prof_total else None},
             "kernels": {nm: {"launches": p.launches, "jobs": p.jobs, "ms": round(p.ms, 4),
