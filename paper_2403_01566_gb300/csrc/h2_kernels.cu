@@ -236,7 +236,7 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-constexpr int QR_MAXPIV = 128;  // largest column count of a pivoted QR
+constexpr int QR_MAXPIV = 256;  // largest column count of a pivoted QR
 
 // Householder QR on a column-major matrix a (rows x cols, leading dimension
 // lda), in place; `a` is global or shared memory.  With piv != nullptr the
@@ -604,20 +604,23 @@ __device__ __forceinline__ int svd_pair_j(int rnd, int p, int ce) {
 }
 
 __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, const SvdJob* __restrict__ jobs,
-                                             int64_t first, int smem_doubles) {
+                                             int64_t first, int smem_doubles, int cmax) {
   const ExecCtx& x = *px;
-  extern __shared__ double sm[];
+  extern __shared__ double sdyn[];
   __shared__ int rotated;
   __shared__ int nrot;
   __shared__ int nround;
-  __shared__ double nrm2[SVD_MAXDIM];
-  __shared__ double dsc[SVD_MAXDIM], dinv[SVD_MAXDIM];  // column scales d and 1/d of M = Mt diag(d)
-  __shared__ double part[256];                          // partial dot products (blockDim <= 256)
-  __shared__ int rlist[SVD_MAXDIM / 2];                 // rotating pairs of the round: (i << 8) | j
-  __shared__ double rfa[SVD_MAXDIM / 2], rfb[SVD_MAXDIM / 2];
-  __shared__ double snorm[SVD_MAXDIM];
-  __shared__ int spos[SVD_MAXDIM];
+  __shared__ double part[256];  // partial dot products (blockDim <= 256)
   __shared__ double s_fro;
+  double* nrm2 = sdyn;                 // squared column norms
+  double* dsc = nrm2 + cmax;           // column scales d of M = Mt diag(d)
+  double* dinv = dsc + cmax;           // 1/d
+  double* snorm = dinv + cmax;         // singular values
+  double* rfa = snorm + cmax;          // rotation factors of the round's rotating pairs
+  double* rfb = rfa + (cmax / 2 + 1);
+  int* spos = reinterpret_cast<int*>(rfb + (cmax / 2 + 1));  // sorted position of each column
+  int* rlist = spos + cmax;            // rotating pairs of the round: (i << 16) | j
+  double* sm = sdyn + svd_colarr_doubles(cmax);
   const SvdJob& J = jobs[blockIdx.x];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
   int* rank_out = (J.rank_slot >= 0) ? x.slot + J.rank_slot : nullptr;
@@ -631,7 +634,7 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
     }
     return;
   }
-  if (rows > SVD_MAXDIM || cols > SVD_MAXDIM) {
+  if (rows > SVD_MAXDIM || cols > cmax || ((int64_t)(rows + 1) * cols > smem_doubles && !J.trans)) {
     if (threadIdx.x == 0) {
       set_err(x, -9);
       if (rank_out) *rank_out = 0;
@@ -737,7 +740,7 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
             dinv[i] = ei * (q * c);
             dinv[j] = ej * (q * c);
             const int slot = atomicAdd(&nround, 1);
-            rlist[slot] = (i << 8) | j;
+            rlist[slot] = (i << 16) | j;
             rfa[slot] = t * dj * ei;
             rfb[slot] = t * di * ej;
           }
@@ -750,8 +753,8 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
         for (int e = threadIdx.x; e < nr * rows; e += blockDim.x) {
           const int sl = e % nr, r = e / nr;
           const int ij = rlist[sl];
-          double* mi = M + (ij >> 8) * ldm;
-          double* mj = M + (ij & 255) * ldm;
+          double* mi = M + (ij >> 16) * ldm;
+          double* mj = M + (ij & 0xffff) * ldm;
           const double u = mi[r], v = mj[r];
           mi[r] = fma(-rfa[sl], v, u);
           mj[r] = fma(rfb[sl], u, v);
@@ -829,35 +832,34 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
 // ||N||_2^2 = lambda_max(G), G = N^T N: Householder tridiagonalisation of G in
 // shared memory (symmetric rank-2 updates), then bisection with Sturm counts on
 // the tridiagonal matrix for its largest eigenvalue.
-__global__ void __launch_bounds__(256) k_norm(const ExecCtx* __restrict__ px, const NormJob* __restrict__ jobs) {
+// G lives in dynamic shared memory sized for the stage's largest n (nmax x
+// (nmax+1) doubles); N is read from global memory (L1-resident).
+__global__ void __launch_bounds__(256) k_norm(const ExecCtx* __restrict__ px, const NormJob* __restrict__ jobs,
+                                              int nmax) {
   const ExecCtx& x = *px;
-  constexpr int NM = GT;  // n <= 64
-  extern __shared__ double sm[];
-  double* Ns = sm;                  // NM x (NM+1)
-  double* G = sm + NM * (NM + 1);   // NM x (NM+1)
+  constexpr int NM = NORM_MAXN;
+  extern __shared__ double G[];  // nmax x (nmax+1)
   __shared__ double v[NM], p[NM], w[NM], d[NM], e[NM];
   __shared__ double red[32];
   __shared__ double sh[4];
   const NormJob& J = jobs[blockIdx.x];
   const int n = dimv(J.n, x.slot);
-  if (n <= 0 || n > NM) {
+  if (n <= 0 || n > nmax || n > NM) {
     if (threadIdx.x == 0) {
-      if (n > NM) set_err(x, -9);
+      if (n > 0) set_err(x, -9);
       x.nrm[J.norm_idx] = 0.0;
       x.scal[J.norm_idx] = 0.0;
     }
     return;
   }
   const double* S = ptrv(J.src, x);
-  const int ld = NM + 1;
-  for (int e2 = threadIdx.x; e2 < n * n; e2 += blockDim.x) Ns[(e2 / n) * ld + e2 % n] = S[(int64_t)(e2 / n) * J.lds + e2 % n];
-  __syncthreads();
+  const int ld = nmax + 1;
   // G = N^T N (symmetric)
   for (int e2 = threadIdx.x; e2 < n * n; e2 += blockDim.x) {
     const int i = e2 / n, j = e2 % n;
     if (j < i) continue;
     double a = 0.0;
-    for (int l = 0; l < n; ++l) a = fma(Ns[l * ld + i], Ns[l * ld + j], a);
+    for (int l = 0; l < n; ++l) a = fma(S[(int64_t)l * J.lds + i], S[(int64_t)l * J.lds + j], a);
     G[i * ld + j] = a;
     G[j * ld + i] = a;
   }
@@ -989,7 +991,7 @@ __global__ void k_finalize(const ExecCtx* __restrict__ px) {
 }
 
 // ------------------------------------------------------------- launchers ----
-size_t norm_smem_bytes() { return sizeof(double) * 2 * GT * (GT + 1); }
+size_t norm_smem_bytes(int nmax) { return sizeof(double) * nmax * (nmax + 1); }
 size_t gemm_smem_bytes() { return sizeof(double) * gemm_smem_doubles(GT, GT); }
 size_t svd_smem_bytes(int rows, int cols) { return sizeof(double) * (size_t)(rows + 1) * cols; }
 
@@ -1003,12 +1005,12 @@ cudaError_t kernels_init() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gemm<GQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes());
+  e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes(NORM_MAXN));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_MAX_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)svd_smem_bytes(SVD_MAXDIM, SVD_MAXDIM));
+                           8 * (SVD_SMEM_MATRIX_DOUBLES + svd_colarr_doubles(SVD_MAXDIM)));
   if (e != cudaSuccess) return e;
   g_attr_done = true;
   return cudaSuccess;
@@ -1045,12 +1047,19 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t
       break;
     case ST_SVD:
       {
-      const size_t sm = st.smem > 0 ? (size_t)st.smem : svd_smem;
-      k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first, (int)(sm / 8));
+      // st.aux = largest column count of the stage; st.smem covers its
+      // per-column arrays and the matrix area
+      const int cmax = st.aux > 0 ? st.aux : SVD_MAXDIM;
+      const size_t sm = st.smem > 0 ? (size_t)st.smem : svd_smem + 8 * (size_t)svd_colarr_doubles(cmax);
+      k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first,
+                                      (int)(sm / 8) - svd_colarr_doubles(cmax), cmax);
     }
       break;
     case ST_NORM:
-      k_norm<<<st.count, 256, norm_smem_bytes(), s>>>(x, j.norm + st.first);
+    {
+      const int nmax = st.aux > 0 ? st.aux : NORM_MAXN;
+      k_norm<<<st.count, 256, norm_smem_bytes(nmax), s>>>(x, j.norm + st.first, nmax);
+    }
       break;
     case ST_SCAN:
       k_scan<<<(st.count + 127) / 128, 128, 0, s>>>(x, j.scan + st.first, st.count);

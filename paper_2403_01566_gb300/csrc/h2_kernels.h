@@ -6,7 +6,22 @@
 
 namespace h2 {
 
-constexpr int SVD_MAXDIM = 128;  // largest Jacobi SVD (rows and columns)
+constexpr int SVD_MAXDIM = 256;  // largest Jacobi SVD (rows and columns)
+constexpr int NORM_MAXN = 128;   // largest matrix of a spectral-norm job
+constexpr int SVD_SMEM_MATRIX_DOUBLES = 129 * 64;  // SVD matrices up to this size sit in shared memory
+
+#ifdef __CUDACC__
+#define H2_HOST_DEVICE __host__ __device__
+#else
+#define H2_HOST_DEVICE
+#endif
+// Per-column arrays of an SVD stage whose jobs have at most cmax columns, in
+// doubles: nrm2, dsc, dinv, snorm (cmax each), rfa, rfb (cmax/2+1 each), spos
+// and rlist (ints: cmax + cmax/2+1, two per double).  They precede the matrix
+// area in the stage's dynamic shared memory.
+H2_HOST_DEVICE constexpr int svd_colarr_doubles(int cmax) {
+  return 4 * cmax + 2 * (cmax / 2 + 1) + (cmax + cmax / 2 + 2) / 2 + 1;
+}
 constexpr int GEMM_MAXTILE = 64; // largest GEMM output tile (rows and columns)
 
 // Device copies of the job arrays of a stage list.

@@ -248,19 +248,28 @@ struct Builder {
     if (sv.empty()) return;
     // shared memory for the largest job, capped at 129 x 64 doubles (66 KB,
     // three CTAs per SM); larger jobs run in place in global memory
-    const int smem = (int)(sizeof(double) * std::min<size_t>((size_t)(sv_maxr + 1) * sv_maxc, 129 * 64));
+    const int smem = (int)(sizeof(double) *
+                           (std::min<size_t>((size_t)(sv_maxr + 1) * sv_maxc, SVD_SMEM_MATRIX_DOUBLES) +
+                            svd_colarr_doubles(sv_maxc)));
     largest_first(sv, sv_cost);
     sv_cost.clear();
-    P.stages.push_back(Stage{ST_SVD, (int64_t)P.svd.size(), (int)sv.size(), tag, smem});
+    P.stages.push_back(Stage{ST_SVD, (int64_t)P.svd.size(), (int)sv.size(), tag, smem, sv_maxc});
     P.svd.insert(P.svd.end(), sv.begin(), sv.end());
     sv.clear();
     sv_maxr = sv_maxc = 1;
   }
+  int nj_nmax = 1;  // largest n of the pending norm jobs
+  void norm(Ptr src, int lds, DimV n, int norm_idx) {
+    if (n.max > NORM_MAXN) throw std::runtime_error("norm matrix too large");
+    nj.push_back(NormJob{src, lds, n.d(), norm_idx});
+    nj_nmax = std::max(nj_nmax, n.max);
+  }
   void flush_norm(int tag) {
     if (nj.empty()) return;
-    P.stages.push_back(Stage{ST_NORM, (int64_t)P.norm.size(), (int)nj.size(), tag, 0});
+    P.stages.push_back(Stage{ST_NORM, (int64_t)P.norm.size(), (int)nj.size(), tag, 0, nj_nmax});
     P.norm.insert(P.norm.end(), nj.begin(), nj.end());
     nj.clear();
+    nj_nmax = 1;
   }
   void scan(const std::vector<int>& in_slots, int out_first) {
     sc.push_back(ScanJob{(int)P.idx.size(), (int)in_slots.size(), out_first});
@@ -959,7 +968,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     std::vector<Factor> colf(aggs.size());
     int max_steps = 0;
     for (auto& a : aggs) max_steps = std::max(max_steps, 2 * ((1 << a.d) - 1));
-    const int AGGC = 2 * AGGM;
+    const int AGGC = 2 * std::max(MB, AGGM);  // widest merged factor pair
     for (size_t a = 0; a < aggs.size(); ++a) {
       const int n = 1 << aggs[a].d;
       for (int i = 0; i < n; ++i) rowf[a].push_back(cell_factor(V[aggs[a].cells[(size_t)i * n]]));
@@ -1051,12 +1060,12 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         const int m1 = J.f1.m.max, m2 = J.f2.m.max;
         if (!J.vertical) {
           // Gc = [L1 rho1^T, L2 rho2^T]
-          B.tiles(PT(AR_WS, s.Gc), AGGC, J.f1.rows_t, J.f1.m, 0, [&](int r0, int, int, Dim) {
-            B.term2(rows_of(J.f1.L, r0), mref(PT(AR_WS, s.rho1), m1, 1), J.f1.m.d());
+          B.tiles(PT(AR_WS, s.Gc), AGGC, J.f1.rows_t, J.f1.m, 0, [&](int r0, int, int c0, Dim) {
+            B.term2(rows_of(J.f1.L, r0), mref(PT(AR_WS, s.rho1 + (int64_t)c0 * m1), m1, 1), J.f1.m.d());
           });
           Ptr o2 = pdyn(PT(AR_WS, s.Gc + J.f1.m.c), J.f1.m.s, 1);
-          B.tiles(o2, AGGC, J.f1.rows_t, J.f2.m, 0, [&](int r0, int, int, Dim) {
-            B.term2(rows_of(J.f2.L, r0), mref(PT(AR_WS, s.rho2), m2, 1), J.f2.m.d());
+          B.tiles(o2, AGGC, J.f1.rows_t, J.f2.m, 0, [&](int r0, int, int c0, Dim) {
+            B.term2(rows_of(J.f2.L, r0), mref(PT(AR_WS, s.rho2 + (int64_t)c0 * m2), m2, 1), J.f2.m.d());
           });
         } else {
           // Gc = [L1 rho[:, :m1]^T; L2 rho[:, m1:]^T], rho is (m1+m2) x (m1+m2)
@@ -1214,14 +1223,20 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         B.term2(rows_of(F.f.R, r0), mref(PT(AR_WS, F.rhoL + (int64_t)c0 * MB), MB, 1), F.f.m.d());
       });
       nm[i] = B.alloc((int64_t)MB * MB);
-      if (F.f.m.max > GEMM_MAXTILE) throw std::runtime_error("factor width above tile");
-      B.out(PT(AR_WS, nm[i]), MB, F.f.m.d(), F.f.m.d(), 0);
-      B.term2(mref(PT(AR_WS, F.rhoL), MB), mref(PT(AR_WS, F.rhoR), MB, 1), F.f.m.d());
+      B.tiles(PT(AR_WS, nm[i]), MB, F.f.m.max, F.f.m, 0, [&](int r0, int nr, int c0, Dim) {
+        if (F.f.m.s >= 0) {
+          // dynamic width (<= 64): one tile, rows clamped to the rank
+          B.go.back().m = F.f.m.d();
+        }
+        (void)nr;
+        B.term2(mref(PT(AR_WS, F.rhoL + (int64_t)r0 * MB), MB),
+                mref(PT(AR_WS, F.rhoR + (int64_t)c0 * MB), MB, 1), F.f.m.d());
+      });
     }
     B.flush_gemm(TAG_COND);
     for (size_t i = 0; i < fin.size(); ++i) {
       Final& F = fin[i];
-      B.nj.push_back(NormJob{PT(AR_WS, nm[i]), MB, F.f.m.d(), F.nidx});
+      B.norm(PT(AR_WS, nm[i]), MB, F.f.m, F.nidx);
     }
     B.flush_norm(TAG_COND);
     (void)mark;
@@ -1270,6 +1285,16 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   auto rho = [&](const Side& S, const Final& F) { return S.rowside ? F.rhoR : F.rhoL; };
   auto Gcond = [&](const Side& S, const Final& F) { return S.rowside ? F.Gc : F.Gcc; };
   const double tol_mult = 1.0;
+  // GEMM output columns of a factor width: dynamic widths (<= 64) in one tile,
+  // static ones in tiles of GEMM_MAXTILE
+  auto col_tiles = [&](const DimV& m, const std::function<void(int, Dim)>& emit) {
+    if (m.s >= 0) {
+      if (m.max > GEMM_MAXTILE) throw std::runtime_error("dynamic factor width above tile");
+      emit(0, m.d());
+      return;
+    }
+    for (int c0 = 0; c0 < m.c; c0 += GEMM_MAXTILE) emit(c0, DC(std::min(GEMM_MAXTILE, m.c - c0)));
+  };
   // phase 0: panel widths (prefix sums of the factor widths)
   auto ph_scan = [&](Side& S, int l) {
     const Tree& T = *S.T;
@@ -1320,9 +1345,11 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
           for (int h = 0; h < 2; ++h) {
             const int ch = Tree::child(c, h);
             Ptr d2 = h == 0 ? dst : pdyn(dst, S.rank[Tree::child(c, 0)], S.wmax[c]);
-            B.out(d2, S.wmax[c], DS(S.rank[ch]), F.f.m.d(), 0);
-            B.term2(mref(PT(AR_WS, S.lam.at({ch, S.star[c][i]})), MB), mref(PT(AR_WS, rho(S, F)), MB, 1), F.f.m.d(),
-                    w, F.nidx);
+            col_tiles(F.f.m, [&](int c0, Dim wdim) {
+              B.out(padd(d2, c0), S.wmax[c], DS(S.rank[ch]), wdim, 0);
+              B.term2(mref(PT(AR_WS, S.lam.at({ch, S.star[c][i]})), MB),
+                      mref(PT(AR_WS, rho(S, F) + (int64_t)c0 * MB), MB, 1), F.f.m.d(), w, F.nidx);
+            });
           }
         }
       }
@@ -1381,18 +1408,21 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         const Final& F = fin[b];
         const int64_t o = B.alloc((int64_t)KP * MB);
         S.lam[{c, b}] = o;
-        B.out(PT(AR_WS, o), MB, DS(S.rank[c]), F.f.m.d(), 0);
-        if (T.leaf(c)) {
-          const int tb = blk_cluster(S, F);
-          MRef Lr = rows_of(fac_rows(S, F), T.off[c] - T.off[tb]);
-          B.term2(mref(PT(AR_C, S.offBasis + (int64_t)T.off[c] * KP), KP, 1), Lr, DC(T.size[c]));
-        } else {
-          for (int h = 0; h < 2; ++h) {
-            const int ch = Tree::child(c, h);
-            B.term2(mref(PT(AR_C, S.offTrans + (int64_t)ch * KP * KP), KP, 1), mref(PT(AR_WS, S.lam.at({ch, b})), MB),
-                    DS(S.rank[ch]));
+        col_tiles(F.f.m, [&](int c0, Dim wdim) {
+          B.out(PT(AR_WS, o + c0), MB, DS(S.rank[c]), wdim, 0);
+          if (T.leaf(c)) {
+            const int tb = blk_cluster(S, F);
+            MRef Lr = rows_of(fac_rows(S, F), T.off[c] - T.off[tb]);
+            Lr.p = padd(Lr.p, c0);
+            B.term2(mref(PT(AR_C, S.offBasis + (int64_t)T.off[c] * KP), KP, 1), Lr, DC(T.size[c]));
+          } else {
+            for (int h = 0; h < 2; ++h) {
+              const int ch = Tree::child(c, h);
+              B.term2(mref(PT(AR_C, S.offTrans + (int64_t)ch * KP * KP), KP, 1),
+                      mref(PT(AR_WS, S.lam.at({ch, b}) + c0), MB), DS(S.rank[ch]));
+            }
           }
-        }
+        });
       }
     }
   };

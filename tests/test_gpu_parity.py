@@ -47,6 +47,10 @@ CASES = [
     (I.grid_2d(64), 1e-6),                       # several tiles and agglomeration depths
     (I.square_2d(1500, seed=7, leaf=32, order=3), 1e-6),
     (I.cube_3d(1200, seed=11, leaf=40, order=2), 1e-4),
+    # k = 64 (3D, order 4): factor widths 2k = 128, merges 256 wide
+    (I.sphere_3d(2048), 1e-6),
+    (I.sphere_3d(2048), 1e-4),
+    (I.cube_3d(2048, seed=13, leaf=64, order=4), 1e-6),
 ]
 
 
