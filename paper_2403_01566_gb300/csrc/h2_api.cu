@@ -135,7 +135,7 @@ static int upload_plan(PlanRT& rt, const std::vector<int>& rank_src) {
   rt.d_nrm = rt.d_scal + P.nscal;
   rt.d_slot = (int*)(rt.d_nrm + P.nscal);
   rt.d_err = rt.d_slot + nslot;
-  CK(cudaMalloc(&rt.d_ws, std::max<int64_t>(P.ws_len, 1) * sizeof(double)));
+  CK(cudaMalloc(&rt.d_ws, std::max<int64_t>(P.ws_len + P.fac_len, 1) * sizeof(double)));
   rt.svd_smem = svd_smem_bytes(P.svd_maxrows, P.svd_maxcols);
   CK(cudaEventCreateWithFlags(&rt.last, cudaEventDisableTiming));
   return H2_OK;
@@ -170,6 +170,7 @@ static int run_plan(PlanRT& rt, double* bx, double* by, double* bc, int* out_int
   ctx.base[AR_Y] = by;
   ctx.base[AR_C] = bc;
   ctx.base[AR_K] = rt.d_konst;
+  ctx.base[AR_F] = rt.d_ws + P.ws_len;
   ctx.slot = rt.d_slot;
   ctx.scal = rt.d_scal;
   ctx.nrm = rt.d_nrm;
@@ -227,6 +228,7 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
   ctx.base[AR_Y] = by;
   ctx.base[AR_C] = bc;
   ctx.base[AR_K] = rt.d_konst;
+  ctx.base[AR_F] = rt.d_ws + P.ws_len;
   ctx.slot = rt.d_slot;
   ctx.scal = rt.d_scal;
   ctx.nrm = rt.d_nrm;
@@ -585,7 +587,7 @@ static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   C->arena_len = C->off_WF + (int64_t)(C->cols->depth + 1) * C->cols->n * P.kpad;
   C->nagglomerated = P.nagg;
   C->launches = (int)P.stages.size() + 1;
-  C->workspace_bytes = P.ws_len * 8;
+  C->workspace_bytes = (P.ws_len + P.fac_len) * 8;
   C->uid = ++g_uid;
   C->stream = s;
   if (cudaMallocAsync(&C->d_arena, C->arena_len * sizeof(double), s) != cudaSuccess ||

@@ -17,8 +17,10 @@
 namespace h2 {
 
 // AR_WS per-product workspace, AR_X / AR_Y the factors, AR_C the product,
-// AR_K constants of the plan (identity matrices).
-enum Arena : int { AR_WS = 0, AR_X = 1, AR_Y = 2, AR_C = 3, AR_K = 4, AR_NONE = -1, AR_COUNT = 5 };
+// AR_K constants of the plan (identity matrices), AR_F the explicit factors of
+// the terminal blocks (kept while the workspace of the accumulation phases is
+// reused by the recompression phases).
+enum Arena : int { AR_WS = 0, AR_X = 1, AR_Y = 2, AR_C = 3, AR_K = 4, AR_F = 5, AR_NONE = -1, AR_COUNT = 6 };
 
 // value = c + slot[s1] + slot[s2] (s1/s2 < 0: absent), then, if mc >= 0,
 // min(value, mc + slot[ms]) (ms < 0: absent).

@@ -119,6 +119,12 @@ struct Builder {
     ws_peak = std::max(ws_peak, ws);
     return o;
   }
+  int64_t fac = 0;  // bump pointer of the terminal-factor arena
+  int64_t falloc(int64_t n) {
+    const int64_t o = fac;
+    fac += (std::max<int64_t>(n, 1) + 31) & ~int64_t(31);
+    return o;
+  }
   int slot(int init) {
     P.slot_init.push_back(init);
     return (int)P.slot_init.size() - 1;
@@ -359,7 +365,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   auto XVF = [&](int lvl, int row) { return mref(PT(AR_X, X.off_VF + ((int64_t)lvl * TI.n + row) * k), k); };
   auto YWF = [&](int lvl, int row) { return mref(PT(AR_Y, Y.off_WF + ((int64_t)lvl * TK.n + row) * k), k); };
 
-  // ------------------------------------------------ 1. basis products ----
+    P.stats["ws_before_p1"] = B.ws;
+// ------------------------------------------------ 1. basis products ----
   const int64_t offP = B.alloc((int64_t)TJ.ncl * k * k);
   auto Pm = [&](int s, int t = 0) { return mref(PT(AR_WS, offP + (int64_t)s * k * k), k, t); };
   for (int s = Tree::first(D); s < TJ.ncl; ++s) {
@@ -378,6 +385,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     B.flush_gemm(TAG_P);
   }
 
+  P.stats["ws_before_p2"] = B.ws;
   // ------------------------------------- 2. product tree (symbolic) ----
   std::vector<std::pair<int, int>> case1, case2, case3;
   std::unordered_set<int64_t> hasP;
@@ -464,6 +472,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     }
   }
 
+  P.stats["ws_before_p3"] = B.ws;
   // ---------------------------- 3. precomputed leaf products, S-hat ----
   std::unordered_map<int, int64_t> offQx, offNx, offQy, offNy;
   for (int x : useQx) {
@@ -518,6 +527,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     B.flush_gemm(TAG_SHAT);
   }
 
+  P.stats["ws_before_p4"] = B.ws;
   // ------------------------------------------------------- 4. records ----
   std::unordered_map<int64_t, MRef> RA, RAn, RB, RBn;
   for (auto& [key, list] : recA) {
@@ -554,6 +564,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   P.stats["recA"] = RA.size() + RAn.size();
   P.stats["recB"] = RB.size() + RBn.size();
 
+  P.stats["ws_before_p5"] = B.ws;
   // ------------------------------------------- 5. target / visited tree ----
   P.cblocks = std::make_shared<BlockTree>();
   BlockTree& BC = *P.cblocks;
@@ -657,6 +668,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     V[it->second].dense = true;
   }
 
+  P.stats["ws_before_p6"] = B.ws;
   // ------------------------------------------------ 6. Omega pushes ----
   // Omega(u, r) = rec(u, r) + Omega(u, parent r) F_{Y,r}^*  (A side, column tree T_K)
   // OmegaB(v, t) = recB(v, t) + OmegaB(v, parent t) E_{X,t}^*  (B side, row tree T_I)
@@ -758,6 +770,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     B.flush_gemm(TAG_OMEGA);
   }
 
+  P.stats["ws_before_p7"] = B.ws;
   // ---------------------------------------- 7. root coefficient pushes ----
   // ahat_q = E_{X,t} ahat_parent F_{Y,r}^* + Omega(t, r);  bhat mirror.
   {
@@ -790,6 +803,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     }
   }
 
+  P.stats["ws_before_p8"] = B.ws;
   // ------------------------- 8. deep pushes and explicit A_tr, B_tr -----
   // Buffers: semi-uniform terminals get L = [A, V_{X,t}] (|t| x 2k) and
   // R = [W_{Y,r}, B] (|r| x 2k); dense terminals get A (|t| x k), B (|r| x k).
@@ -799,16 +813,16 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     const int nt = TI.size[n.t], nr = TK.size[n.r];
     const bool dense = n.dense || n.kind == VK_OUT;
     if (!dense) {
-      const int64_t oL = B.alloc((int64_t)nt * 2 * k), oR = B.alloc((int64_t)nr * 2 * k);
-      n.L = mref(PT(AR_WS, oL), 2 * k);
-      n.R = mref(PT(AR_WS, oR), 2 * k);
-      n.A = mref(PT(AR_WS, oL), 2 * k);
-      n.Bm = mref(PT(AR_WS, oR + k), 2 * k);
+      const int64_t oL = B.falloc((int64_t)nt * 2 * k), oR = B.falloc((int64_t)nr * 2 * k);
+      n.L = mref(PT(AR_F, oL), 2 * k);
+      n.R = mref(PT(AR_F, oR), 2 * k);
+      n.A = mref(PT(AR_F, oL), 2 * k);
+      n.Bm = mref(PT(AR_F, oR + k), 2 * k);
       B.copy(XVF(n.level, TI.off[n.t]).p, k, padd(n.L.p, k), 2 * k, DC(nt), DC(k), 0);
       B.copy(YWF(n.level, TK.off[n.r]).p, k, n.R.p, 2 * k, DC(nr), DC(k), 0);
     } else {
-      n.A = mref(PT(AR_WS, B.alloc((int64_t)nt * k)), k);
-      n.Bm = mref(PT(AR_WS, B.alloc((int64_t)nr * k)), k);
+      n.A = mref(PT(AR_F, B.falloc((int64_t)nt * k)), k);
+      n.Bm = mref(PT(AR_F, B.falloc((int64_t)nr * k)), k);
     }
   }
   B.flush_copy(TAG_EXPAND);
@@ -891,6 +905,13 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     B.flush_gemm(TAG_EXPAND);
   }
 
+  // Everything the accumulation phases left in the workspace (basis products,
+  // S-hat descents, records, Omega/root/deep pushes) is dead now: the
+  // terminal factors in AR_F carry the result on.  The recompression phases
+  // reuse the workspace from its start.
+  P.stats["ws_accumulation"] = B.ws_peak;
+  B.ws = 0;
+  P.stats["ws_before_p9"] = B.ws;
   // --------------------------------------------- 9. dense terminals ----
   // G = sum X|ts Y|sr (case 3) + A W_{Y,r}^* + V_{X,t} B^*
   // (inadmissible target leaves are written straight into C's nearfield).
@@ -946,6 +967,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   for (auto& n : V)
     if (n.dense && n.kind != VK_OUT) n.R = mref(PT(AR_K, offI), maxleaf);
 
+  P.stats["ws_before_p10"] = B.ws;
   // ------------------------------------------- 10. agglomeration ----
   struct Factor {
     MRef L, R;
@@ -1163,6 +1185,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     }
   }
 
+  P.stats["ws_before_p11"] = B.ws;
   // ----------------------------------- 11. condensation and norms ----
   struct Final {
     int cb, t, r;
@@ -1243,6 +1266,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     (void)mark2;
   }
 
+  P.stats["ws_before_p12"] = B.ws;
   // --------------------------------------- 12. adaptive cluster bases ----
   // row*(t): final admissible blocks whose row cluster is t or an ancestor.
   // The row and the column basis are independent: their levels run in the
@@ -1451,6 +1475,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   auto& lamR = SR.lam;
   auto& lamC = SC.lam;
 
+  P.stats["ws_before_p13"] = B.ws;
   // --------------------------------------------------- 13. couplings ----
   // S_b = (V_t^* L_b) (W_r^* R_b)^*
   for (size_t i = 0; i < fin.size(); ++i) {
@@ -1462,6 +1487,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   B.flush_gemm(TAG_COUPLE);
 
   P.ws_len = B.ws_peak;
+  P.fac_len = B.fac;
   P.stats["final_adm"] = fin.size();
   P.stats["stages"] = P.stages.size();
   P.stats["gemm_outputs"] = P.gout.size();

@@ -48,6 +48,7 @@ struct Plan {
   std::vector<int> slot_init;
   std::vector<double> konst;     // AR_K contents
   int64_t ws_len = 0;            // doubles
+  int64_t fac_len = 0;           // doubles of the terminal-factor arena (placed after the workspace)
   int nscal = PARAM_COUNT;       // scal/nrm entries (first PARAM_COUNT are parameters)
   int svd_maxrows = 1, svd_maxcols = 1;
   // product layout (valid for product plans)
