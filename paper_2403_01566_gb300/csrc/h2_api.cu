@@ -284,6 +284,7 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
     const Stage& st = P.stages[i];
     pr.jobs += st.count;
     double st_fl = 0.0;
+    double sw_sum = 0.0, sw_max = 0.0, rows_sum = 0.0, cols_sum = 0.0;
     for (int j = 0; j < st.count; ++j) {
       double fl = 0, by = 0;
       const int64_t J = st.first + j;
@@ -344,6 +345,10 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
           // row for each applied rotation
           fl += (r * c * (c - 1) + 2 * r * c) * sweeps[2 * J] + 6 * r * sweeps[2 * J + 1] + 2 * r * c;
           by += 16 * r * c;
+          sw_sum += sweeps[2 * J];
+          sw_max = std::max(sw_max, (double)sweeps[2 * J]);
+          rows_sum += r;
+          cols_sum += c;
           break;
         }
         default:
@@ -353,9 +358,14 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
       pr.bytes += by;
       st_fl += fl;
     }
-    if (verbose)
-      std::fprintf(stderr, "stage %4zu kind %d tag %2d jobs %7d smem %6d ms %9.4f gflop %9.4f tflops %6.3f\n", i,
+    if (verbose) {
+      std::fprintf(stderr, "stage %4zu kind %d tag %2d jobs %7d smem %6d ms %9.4f gflop %9.4f tflops %6.3f", i,
                    st.kind, st.tag, st.count, st.smem, ms, st_fl / 1e9, ms > 0 ? st_fl / ms / 1e9 : 0.0);
+      if (st.kind == ST_SVD && st.count > 0)
+        std::fprintf(stderr, " rows %.1f cols %.1f sweeps %.2f max %.0f", rows_sum / st.count, cols_sum / st.count,
+                     sw_sum / st.count, sw_max);
+      std::fprintf(stderr, "\n");
+    }
   }
   for (auto& e : ev) cudaEventDestroy(e);
   return H2_OK;

@@ -8,7 +8,7 @@ namespace h2 {
 
 constexpr int SVD_MAXDIM = 256;  // largest Jacobi SVD (rows and columns)
 constexpr int NORM_MAXN = 128;   // largest matrix of a spectral-norm job
-constexpr int SVD_SMEM_MATRIX_DOUBLES = 129 * 64;  // SVD matrices up to this size sit in shared memory
+constexpr int SVD_SMEM_MATRIX_DOUBLES = 129 * 64;  // SVD matrices up to this size sit in shared memory (66 KB)
 
 #ifdef __CUDACC__
 #define H2_HOST_DEVICE __host__ __device__

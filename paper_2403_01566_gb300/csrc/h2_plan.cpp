@@ -250,18 +250,20 @@ struct Builder {
     P.svd_maxrows = std::max(P.svd_maxrows, rows);
     P.svd_maxcols = std::max(P.svd_maxcols, cols);
   }
+  // One launch per stage: shared memory for the largest job, capped at 129 x 64
+  // doubles (66 KB, three CTAs per SM); larger jobs run in place in global
+  // memory.  (A separate one-CTA-per-SM launch for the large jobs measured no
+  // faster: it serialises behind the small ones.)
   void flush_svd(int tag) {
     if (sv.empty()) return;
-    // shared memory for the largest job, capped at 129 x 64 doubles (66 KB,
-    // three CTAs per SM); larger jobs run in place in global memory
     const int smem = (int)(sizeof(double) *
-                           (std::min<size_t>((size_t)(sv_maxr + 1) * sv_maxc, SVD_SMEM_MATRIX_DOUBLES) +
+                           (std::min<int64_t>((int64_t)(sv_maxr + 1) * sv_maxc, SVD_SMEM_MATRIX_DOUBLES) +
                             svd_colarr_doubles(sv_maxc)));
     largest_first(sv, sv_cost);
-    sv_cost.clear();
     P.stages.push_back(Stage{ST_SVD, (int64_t)P.svd.size(), (int)sv.size(), tag, smem, sv_maxc});
     P.svd.insert(P.svd.end(), sv.begin(), sv.end());
     sv.clear();
+    sv_cost.clear();
     sv_maxr = sv_maxc = 1;
   }
   int nj_nmax = 1;  // largest n of the pending norm jobs
