@@ -72,7 +72,14 @@ typedef struct {
  *              (binary trees); 0 selects 1/4
  *   max_rank   cap on the adaptive ranks (storage padding of C), <= 64; 0 selects
  *              min(64, max(32, 2k))
- *   precision  0 = FP64 throughout (the only value accepted by this version)
+ *   precision  0 = FP64 throughout;
+ *              1 = FP32 contractions: the accumulation phases (basis products,
+ *                  coupling and nearfield products, splits and pushes; Sections
+ *                  3-4) and the coupling projection (Section 5.2) compute FP32
+ *                  products with FP32 sums from the FP64 data; agglomeration,
+ *                  condensation, QR, SVD, rank decisions and norms stay FP64.
+ *                  Adds about 1e-7 relative rounding to each block; the bound
+ *                  eps still holds for eps >= 1e-6.  Other values: H2_EINVAL.
  *   sync       1 = return after the product is complete and report device errors;
  *              0 = return after enqueueing (errors are reported by h2_check)
  *   stream     cudaStream_t to run on, or NULL for the library stream */

@@ -537,7 +537,8 @@ static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   double theta = (opts && opts->theta > 0.0) ? opts->theta : 0.25;
   if (!(theta < 0.5)) return H2_EINVAL;
   const int max_rank = opts ? opts->max_rank : 0;
-  if (opts && opts->precision != 0) return H2_EINVAL;
+  const int precision = opts ? opts->precision : 0;
+  if (precision != 0 && precision != 1) return H2_EINVAL;
   if (max_rank < 0 || max_rank > GEMM_MAXTILE) return H2_EINVAL;
   const bool sync = opts ? opts->sync != 0 : true;
   cudaStream_t s = (opts && opts->stream) ? (cudaStream_t)opts->stream : g_stream;
@@ -548,7 +549,8 @@ static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   std::shared_ptr<PlanRT> rt;
   {
     std::lock_guard<std::mutex> lk(A->mu);
-    auto key = std::make_pair((const h2_matrix*)B, max_rank * 1000 + (int)std::lround(theta * 997.0));
+    auto key = std::make_pair((const h2_matrix*)B,
+                              (precision * 100 + max_rank) * 1000 + (int)std::lround(theta * 997.0));
     auto it = A->plans.find(key);
     if (it != A->plans.end() && it->second->uid_b == B->uid) {
       rt = std::static_pointer_cast<PlanRT>(it->second->rt);
@@ -557,6 +559,7 @@ static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
       mo.eta = A->eta;
       mo.theta = theta;
       mo.max_rank = max_rank;
+      mo.precision = precision;
       std::shared_ptr<Plan> plan;
       try {
         plan = make_product_plan(desc_of(A), desc_of(B), mo);

@@ -49,20 +49,22 @@ __device__ __forceinline__ double ld_op(const double* p, int ld, int t, int i, i
   return t ? p[(int64_t)j * ld + i] : p[(int64_t)i * ld + j];
 }
 
-// acc[q] += op(A)(m x k) op(B)(k x n) for the outputs of this thread
-template <int Q>
-__device__ __forceinline__ void gemm_accumulate(double (&acc)[Q], int nq, int m, int n, int k, const double* A,
-                                                int lda, int ta, const double* B, int ldb, int tb, double* As,
-                                                double* Bs, int ldbs) {
+// acc[q] += op(A)(m x k) op(B)(k x n) for the outputs of this thread, in the
+// compute type T (double, or float for the FP32 contractions: operands are
+// rounded to FP32 when staged, products and sums are FP32)
+template <int Q, typename T>
+__device__ __forceinline__ void gemm_accumulate(T (&acc)[Q], int nq, int m, int n, int k, const double* A,
+                                                int lda, int ta, const double* B, int ldb, int tb, T* As,
+                                                T* Bs, int ldbs) {
   for (int kk = 0; kk < k; kk += GK) {
     const int kc = min(GK, k - kk);
     for (int e = threadIdx.x; e < m * kc; e += 256) {
       const int r = e / kc, l = e % kc;
-      As[r * (GK + 1) + l] = ld_op(A, lda, ta, r, kk + l);
+      As[r * (GK + 1) + l] = (T)ld_op(A, lda, ta, r, kk + l);
     }
     for (int e = threadIdx.x; e < kc * n; e += 256) {
       const int l = e / n, c = e % n;
-      Bs[l * ldbs + c] = ld_op(B, ldb, tb, kk + l, c);
+      Bs[l * ldbs + c] = (T)ld_op(B, ldb, tb, kk + l, c);
     }
     __syncthreads();
 #pragma unroll
@@ -71,7 +73,7 @@ __device__ __forceinline__ void gemm_accumulate(double (&acc)[Q], int nq, int m,
         const int e = threadIdx.x + 256 * q;
         if (e < m * n) {
           const int r = e / n, c = e % n;
-          double a = acc[q];
+          T a = acc[q];
           for (int l = 0; l < kc; ++l) a = fma(As[r * (GK + 1) + l], Bs[l * ldbs + c], a);
           acc[q] = a;
         }
@@ -90,16 +92,18 @@ __host__ __device__ constexpr int gemm_smem_doubles(int mmax, int nb) {
 }
 
 // Q = outputs per thread (m * n <= 256 Q): small stages take a small Q, so
-// fewer registers and more resident CTAs per SM.
-template <int Q>
+// fewer registers and more resident CTAs per SM.  T = compute type (double;
+// float for the FP32-contraction form).  Inputs and outputs are FP64 arrays.
+template <int Q, typename T>
 __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs,
                                               const GemmTerm* __restrict__ terms, int mmax, int nb) {
   const ExecCtx& x = *px;
-  extern __shared__ double sm[];
+  extern __shared__ double sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   const int ldbs = nb + 1;
-  double* As = sm;                      // mmax x (GK+1)
-  double* Bs = As + mmax * (GK + 1);    // GK x (nb+1)
-  double* Ts = Bs + GK * ldbs;          // mmax x (nb+1)
+  T* As = sm;                      // mmax x (GK+1)
+  T* Bs = As + mmax * (GK + 1);    // GK x (nb+1)
+  T* Ts = Bs + GK * ldbs;          // mmax x (nb+1)
   const GemmOut& O = outs[blockIdx.x];
   const int m = dimv(O.m, x.slot);
   const int n = O.clampn ? min(dimv(O.n, x.slot), GT) : dimv(O.n, x.slot);
@@ -109,46 +113,47 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     return;
   }
   const int nq = (m * n + 255) / 256;
-  double acc[Q];
+  T acc[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) acc[q] = 0.0;
 
   for (int ti = O.t0; ti < O.t1; ++ti) {
-    const GemmTerm& T = terms[ti];
-    double alpha = T.alpha;
-    if (T.scale_idx >= 0) alpha *= x.scal[T.scale_idx];
-    const double* A = ptrv(T.a, x);
-    const double* B = ptrv(T.b, x);
-    const double* C = ptrv(T.c, x);
+    const GemmTerm& Tm = terms[ti];
+    double alpha_d = Tm.alpha;
+    if (Tm.scale_idx >= 0) alpha_d *= x.scal[Tm.scale_idx];
+    const T alpha = (T)alpha_d;
+    const double* A = ptrv(Tm.a, x);
+    const double* B = ptrv(Tm.b, x);
+    const double* C = ptrv(Tm.c, x);
     if (B == nullptr) {  // plain add of op(A) (m x n)
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const int e = threadIdx.x + 256 * q;
-        if (q < nq && e < m * n) acc[q] += alpha * ld_op(A, T.lda, T.ta, e / n, e % n);
+        if (q < nq && e < m * n) acc[q] += alpha * (T)ld_op(A, Tm.lda, Tm.ta, e / n, e % n);
       }
       continue;
     }
-    const int k1 = dimv(T.k1, x.slot);
+    const int k1 = dimv(Tm.k1, x.slot);
     if (C == nullptr) {
-      double tacc[Q];
+      T tacc[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) tacc[q] = 0.0;
-      gemm_accumulate(tacc, nq, m, n, k1, A, T.lda, T.ta, B, T.ldb, T.tb, As, Bs, ldbs);
+      gemm_accumulate(tacc, nq, m, n, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
 #pragma unroll
       for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
       continue;
     }
     // three-factor term: Ts = op(A)op(B) (m x nn), then acc += alpha * Ts op(C)
-    const int nn = dimv(T.k2, x.slot);
+    const int nn = dimv(Tm.k2, x.slot);
     if (nn > nb || m * nn > 256 * Q) {
       if (threadIdx.x == 0) set_err(x, -9);
       return;
     }
     const int nq2 = (m * nn + 255) / 256;
-    double tacc[Q];
+    T tacc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) tacc[q] = 0.0;
-    gemm_accumulate(tacc, nq2, m, nn, k1, A, T.lda, T.ta, B, T.ldb, T.tb, As, Bs, ldbs);
+    gemm_accumulate(tacc, nq2, m, nn, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int e = threadIdx.x + 256 * q;
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
       const int kc = min(GK, nn - kk);
       for (int e = threadIdx.x; e < kc * n; e += 256) {
         const int l = e / n, c = e % n;
-        Bs[l * ldbs + c] = ld_op(C, T.ldc, T.tc, kk + l, c);
+        Bs[l * ldbs + c] = (T)ld_op(C, Tm.ldc, Tm.tc, kk + l, c);
       }
       __syncthreads();
 #pragma unroll
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
           const int e = threadIdx.x + 256 * q;
           if (e < m * n) {
             const int r = e / n, c = e % n;
-            double a = tacc[q];
+            T a = tacc[q];
             for (int l = 0; l < kc; ++l) a = fma(Ts[r * ldbs + kk + l], Bs[l * ldbs + c], a);
             tacc[q] = a;
           }
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     const int e = threadIdx.x + 256 * q;
     if (q < nq && e < m * n) {
       double* p = out + (int64_t)(e / n) * O.ldo + e % n;
-      *p = O.beta ? (*p + acc[q]) : acc[q];
+      *p = O.beta ? (*p + (double)acc[q]) : (double)acc[q];
     }
   }
 }
@@ -999,11 +1004,14 @@ static bool g_attr_done = false;
 
 cudaError_t kernels_init() {
   if (g_attr_done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm<GQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes());
+  cudaError_t e = cudaSuccess;
+  const int gsm = (int)gemm_smem_bytes();
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<4, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<GQ, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<4, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<GQ, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes(NORM_MAXN));
   if (e != cudaSuccess) return e;
@@ -1025,15 +1033,27 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t
   switch (st.kind) {
     case ST_GEMM:
     {
-      const int mmax = st.aux ? (st.aux >> 16) : GT, nb = st.aux ? (st.aux & 0xffff) : GT;
-      const size_t sm = sizeof(double) * gemm_smem_doubles(mmax, nb);
+      const int shape = st.aux & ~GEMM_AUX_FP32;
+      const int mmax = shape ? ((shape >> 16) & 0xff) : GT, nb = shape ? (shape & 0xffff) : GT;
+      const bool f32 = (st.aux & GEMM_AUX_FP32) != 0;
+      const size_t sm = (f32 ? sizeof(float) : sizeof(double)) * gemm_smem_doubles(mmax, nb);
       const int cells = mmax * nb;
-      if (cells <= 256)
-        k_gemm<1><<<st.count, 256, sm, s>>>(x, j.gemm_out + st.first, j.gemm_term, mmax, nb);
-      else if (cells <= 1024)
-        k_gemm<4><<<st.count, 256, sm, s>>>(x, j.gemm_out + st.first, j.gemm_term, mmax, nb);
-      else
-        k_gemm<GQ><<<st.count, 256, sm, s>>>(x, j.gemm_out + st.first, j.gemm_term, mmax, nb);
+      const GemmOut* go = j.gemm_out + st.first;
+      if (f32) {
+        if (cells <= 256)
+          k_gemm<1, float><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
+        else if (cells <= 1024)
+          k_gemm<4, float><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
+        else
+          k_gemm<GQ, float><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
+      } else {
+        if (cells <= 256)
+          k_gemm<1, double><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
+        else if (cells <= 1024)
+          k_gemm<4, double><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
+        else
+          k_gemm<GQ, double><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
+      }
     }
       break;
     case ST_COPY:

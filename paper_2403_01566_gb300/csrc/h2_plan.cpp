@@ -113,6 +113,7 @@ struct Builder {
   std::vector<NormJob> nj;
 
   explicit Builder(Plan& p) : P(p) {}
+  bool fp32_contractions = false;  // precision form 1
   int64_t alloc(int64_t n) {
     const int64_t o = ws;
     ws += (std::max<int64_t>(n, 1) + 31) & ~int64_t(31);
@@ -166,7 +167,11 @@ struct Builder {
       P.gout.push_back(o);
     }
     P.gterm.insert(P.gterm.end(), gt.begin(), gt.end());
-    P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag, 0, (g_mmax << 16) | g_nb});
+    // FP32 contractions: the accumulation phases (basis products, records,
+    // pushes, dense leaf products) and the coupling projection; agglomeration,
+    // condensation and the bases stay FP64
+    const bool f32 = fp32_contractions && (tag <= 9 || tag == 14);  // TAG_P .. TAG_DENSE, TAG_COUPLE
+    P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag, 0, (g_mmax << 16) | g_nb | (f32 ? GEMM_AUX_FP32 : 0)});
     go.clear();
     gt.clear();
     g_mmax = g_nb = 1;
@@ -329,6 +334,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   auto plan = std::make_shared<Plan>();
   Plan& P = *plan;
   Builder B(P);
+  B.fp32_contractions = opt.precision == 1;
   const Tree& TI = *X.rows;
   const Tree& TJ = *X.cols;
   const Tree& TK = *Y.cols;

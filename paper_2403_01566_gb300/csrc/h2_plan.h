@@ -29,6 +29,7 @@ struct MulOptions {
   double eta = 2.0;      // admissibility of the target block tree
   double theta = 0.25;   // weight factor (Section 5.3)
   int max_rank = 0;      // cap of the adaptive ranks (storage padding of C)
+  int precision = 0;     // 0 FP64 throughout; 1 FP32 contractions (accumulation and couplings)
 };
 
 // Indices into the per-product parameter block (ExecCtx::scal[0..]).

@@ -160,21 +160,22 @@ def build(points, kernel, eta, leaf_size, order) -> H2Matrix:
 
 
 def mul(A: H2Matrix, B: H2Matrix, eps: float, max_rank: int = 0, theta: float = 0.0, sync: bool = True,
-        stream=None) -> H2Matrix:
-    """C ~ A*B with block-relative error eps (h2_mul)."""
+        stream=None, precision: int = 0) -> H2Matrix:
+    """C ~ A*B with block-relative error eps (h2_mul); precision 1 = FP32 contractions."""
     o = MulOpts()
-    o.theta, o.max_rank, o.precision, o.sync = float(theta), int(max_rank), 0, 1 if sync else 0
+    o.theta, o.max_rank, o.precision, o.sync = float(theta), int(max_rank), int(precision), 1 if sync else 0
     o.stream = stream
     h = C.c_void_p()
     _check(_lib().h2_mul(A.handle, B.handle, float(eps), C.byref(o), C.byref(h)), "h2_mul")
     return H2Matrix(h.value)
 
 
-def mul_profile(A: H2Matrix, B: H2Matrix, eps: float, prof, max_rank: int = 0, stream=None) -> H2Matrix:
+def mul_profile(A: H2Matrix, B: H2Matrix, eps: float, prof, max_rank: int = 0, stream=None,
+                precision: int = 0) -> H2Matrix:
     """h2_mul_profile: the product with per-kernel-kind device times and work in `prof`
     (an array of 8 KernelProf)."""
     o = MulOpts()
-    o.theta, o.max_rank, o.precision, o.sync = 0.0, int(max_rank), 0, 1
+    o.theta, o.max_rank, o.precision, o.sync = 0.0, int(max_rank), int(precision), 1
     o.stream = stream
     h = C.c_void_p()
     _check(_lib().h2_mul_profile(A.handle, B.handle, float(eps), C.byref(o), prof, C.byref(h)), "h2_mul_profile")

@@ -1,0 +1,82 @@
+"""The FP32-contraction form (h2_mul precision = 1) against the FP64 oracle.
+
+The accumulation phases and the coupling projection compute FP32 products with
+FP32 sums; agglomeration, condensation, QR, SVD, rank decisions and norms stay
+FP64.  Requirements checked:
+
+- the per-block bound ||C_b - (AB)_b||_2 <= eps ||(AB)_b||_2 against the exact
+  dense product, as for the FP64 form;
+- agreement with the FP64 oracle within eps block-relative (both forms are
+  within eps of the exact product; the FP32 rounding itself is ~1e-7);
+- the error of each result against the oracle is printed (pytest -s).
+
+The rank decisions see the FP32 rounding, so ranks may differ from the
+oracle's by a few where a singular value sits near the threshold; they are
+compared only loosely (within 25% per cluster).
+"""
+import numpy as np
+import pytest
+
+from oracle import h2oracle as O
+from paper_2403_01566_gb300 import inputs as I
+from tests.oracle_cases import build_pair
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2403_01566_gb300 import h2  # noqa: E402
+
+CASES = [
+    (I.plain_1d(1024), 1e-6),
+    (I.grid_2d(64), 1e-6),
+    (I.grid_2d(64), 1e-4),
+    (I.sphere_3d(2048), 1e-6),
+    (I.cube_3d(2048, seed=13, leaf=64, order=4), 1e-6),
+]
+
+
+def _blockrel(Cg, Co, Z, blocks):
+    wo = wz = 0.0
+    for b in O.block_leaves(blocks):
+        ix = np.ix_(b.t.idx, b.s.idx)
+        nz = np.linalg.norm(Z[ix], 2) or 1.0
+        wo = max(wo, np.linalg.norm(Cg[ix] - Co[ix], 2) / nz)
+        wz = max(wz, np.linalg.norm(Cg[ix] - Z[ix], 2) / nz)
+    return wo, wz
+
+
+@pytest.mark.parametrize("w,eps", CASES, ids=[f"{w.name}-{e:g}" for w, e in CASES])
+def test_fp32_contractions_within_eps(w, eps):
+    A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
+    B = h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order)
+    C32 = h2.mul(A, B, eps, precision=1)
+    C64 = h2.mul(A, B, eps, precision=0)
+    X, Y = build_pair(w)
+    res = O.multiply(X, Y, eps)
+    Z = X.dense() @ Y.dense()
+    d_oracle, d_exact = _blockrel(C32.to_dense(), res.C.dense(), Z, res.C.blocks)
+    d64, _ = _blockrel(C64.to_dense(), res.C.dense(), Z, res.C.blocks)
+    print(f"\n{w.name} eps={eps:g}: FP32-contraction form vs oracle {d_oracle:.3e}, vs exact {d_exact:.3e}; "
+          f"FP64 form vs oracle {d64:.3e}")
+    assert d_exact <= eps, d_exact
+    assert d_oracle <= eps, d_oracle
+    assert d64 <= 1e-10, d64
+    rr, rc = C32.ranks()
+    ro = np.array([res.ranks_row[c.id] for c in O.all_clusters(X.rows)])
+    co = np.array([res.ranks_col[c.id] for c in O.all_clusters(Y.cols)])
+    assert np.all(np.abs(np.asarray(rr) - ro) <= np.maximum(2, 0.25 * ro))
+    assert np.all(np.abs(np.asarray(rc) - co) <= np.maximum(2, 0.25 * co))
+
+
+def test_precision_values():
+    w = I.plain_1d(256)
+    A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
+    with pytest.raises(h2.H2Error):
+        h2.mul(A, A, 1e-6, precision=2)
+    # the FP64 and FP32 forms have separate cached plans
+    C1 = h2.mul(A, A, 1e-6, precision=1)
+    C0 = h2.mul(A, A, 1e-6, precision=0)
+    assert np.isfinite(C1.to_dense()).all() and np.isfinite(C0.to_dense()).all()
