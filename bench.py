@@ -126,22 +126,46 @@ def oracle_subprocess(grid, eps, nprod):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself for one process)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, max_total_ms):
+    """Products per second of all ranks together: every rank runs `steps`
+    independent products (replicas), the job takes the slowest rank's time."""
+    return world * steps / (max_total_ms / 1e3)
+
+
+REFERENCE_BUDGET_S = 180.0  # the reference arm stops taking steps after this much oracle time
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    # warm-up on a small grid, then one full product per timed step budget
-    oracle_subprocess(16, EPS, 1)
-    nprod = 1
-    ts = oracle_subprocess(GRID, EPS, nprod)
+    # warm-up: W products on a 16 x 16 grid (imports, BLAS start-up); timed
+    # steps: one full product of the workload each, at most K, stopping once
+    # the oracle time passes REFERENCE_BUDGET_S
+    oracle_subprocess(16, EPS, max(1, args.warmup))
+    ts = []
+    while len(ts) < max(1, args.steps) and sum(ts) < REFERENCE_BUDGET_S:
+        ts += oracle_subprocess(GRID, EPS, 1)
+    nprod = len(ts)
     value = nprod / sum(ts)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": nprod,
-        "warmup": 1, "ms_per_step": 1e3 * sum(ts) / nprod, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "warmup": max(1, args.warmup), "ms_per_step": 1e3 * sum(ts) / nprod, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": workload_config(),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{nprod} full product(s) of the workload on one host thread "
-                                   "(numpy FP64 oracle, input build excluded); warm-up on a 16x16 grid"},
+                                   f"(numpy FP64 oracle, input build excluded; at most {args.steps} steps, "
+                                   f"stopping after {REFERENCE_BUDGET_S:.0f} s); warm-up on a 16x16 grid"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -216,12 +240,8 @@ def main():
     for C in outs:
         C.check()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    value = whole_job_rate(world, args.steps, total_ms)
     launches = outs[0].info().launches * args.steps
     st0 = outs[0].info()
     for C in outs:
