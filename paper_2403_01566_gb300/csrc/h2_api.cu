@@ -1,7 +1,8 @@
 // C ABI of the library (include/h2.h): handle management, device upload of
 // the inputs, and execution of the planned stage lists on the GPU.
 //
-// A product plan is built once per (X, Y, options) and cached in X; its stage
+// A product plan is built once per operand structure and options and kept in
+// a small LRU cache shared by all operand pairs of that structure; its stage
 // list is captured into a CUDA graph on first use and replayed afterwards.
 // The graph reads every pointer from a per-plan device control block
 // (ExecCtx), which is rewritten before each replay.
@@ -12,10 +13,12 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <list>
 #include <string>
 #include <vector>
 
 #include "../../include/h2.h"
+#include "h2_assemble.h"
 #include "h2_build.h"
 #include "h2_internal.h"
 #include "h2_kernels.h"
@@ -27,6 +30,10 @@ static thread_local std::string g_last_cuda;
 
 static int cuda_fail(cudaError_t e, const char* where) {
   g_last_cuda = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // allocation failures are not sticky: clear and report
+    return H2_ENOMEM;
+  }
   return H2_ECUDA;
 }
 #define CK(call)                                        \
@@ -85,6 +92,7 @@ struct PlanRT {
   cudaEvent_t ring_ev[RING] = {};
   int ring_next = 0;
   ~PlanRT() {
+    if (last) cudaEventSynchronize(last);  // the last replay may still use the workspace
     if (graph) cudaGraphExecDestroy(graph);
     if (last) cudaEventDestroy(last);
     for (auto& e : ring_ev)
@@ -398,6 +406,67 @@ static MatDesc desc_of(const h2_matrix* A) {
 }
 
 // Explicit level bases of a matrix (needed when it is a factor or expanded).
+// Structure signature of a matrix: everything a product plan depends on
+// (trees, block tree, padded rank, arena layout, admissibility); the numeric
+// contents are reached through the arena base pointers at replay time.
+static uint64_t matrix_sig(const h2_matrix* M) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  uint64_t eta_bits;
+  std::memcpy(&eta_bits, &M->eta, sizeof eta_bits);
+  mix(M->rows->hash);
+  mix(M->cols->hash);
+  mix(M->blocks->sig);
+  mix((uint64_t)M->kpad);
+  mix((uint64_t)M->dim);
+  mix(eta_bits);
+  mix((uint64_t)M->same_basis);
+  for (int64_t v : {M->off_V, M->off_E, M->off_W, M->off_F, M->off_S, M->off_N, M->off_VF, M->off_WF, M->arena_len})
+    mix((uint64_t)v);
+  return h;
+}
+
+// Product plans (with their device job arrays, workspace and graph), shared
+// by every operand pair of the same structure; least recently used first out.
+struct PlanKey {
+  uint64_t a, b;
+  int opt;
+  bool operator==(const PlanKey& o) const { return a == o.a && b == o.b && opt == o.opt; }
+};
+constexpr size_t PLAN_CACHE_MAX = 4;
+std::mutex g_plans_mu;
+std::list<std::pair<PlanKey, std::shared_ptr<PlanRT>>> g_plans;  // most recent first
+
+static std::shared_ptr<PlanRT> plan_lookup(const PlanKey& k) {
+  std::lock_guard<std::mutex> lk(g_plans_mu);
+  for (auto it = g_plans.begin(); it != g_plans.end(); ++it)
+    if (it->first == k) {
+      g_plans.splice(g_plans.begin(), g_plans, it);
+      return g_plans.front().second;
+    }
+  return nullptr;
+}
+
+static void plan_insert(const PlanKey& k, std::shared_ptr<PlanRT> rt) {
+  std::shared_ptr<PlanRT> evicted;
+  {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    g_plans.emplace_front(k, std::move(rt));
+    if (g_plans.size() > PLAN_CACHE_MAX) {
+      evicted = std::move(g_plans.back().second);  // released outside the lock
+      g_plans.pop_back();
+    }
+  }
+}
+
+static void plan_cache_clear() {
+  std::list<std::pair<PlanKey, std::shared_ptr<PlanRT>>> old;
+  {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    old.swap(g_plans);
+  }
+}
+
 static int ensure_level_bases(h2_matrix* A, cudaStream_t s) {
   if (A->levels_ready) return H2_OK;
   const double params[PARAM_COUNT] = {0.0, 0.0};
@@ -469,27 +538,33 @@ int h2_build(const double* points, int64_t n, const h2_build_opts* o, h2_matrix*
     A->cols = A->rows;
     A->blocks = std::make_shared<BlockTree>();
     build_block_tree(*A->rows, *A->cols, o->eta, *A->blocks);
-    HostH2 H;
-    assemble_chebyshev(points, *A->rows, *A->blocks, o->order, o->kernel, o->kparam, H);
     const Tree& T = *A->rows;
+    const BlockTree& BT = *A->blocks;
     A->same_basis = true;
     A->off_V = 0;
-    A->off_E = A->off_V + (int64_t)H.V.size();
-    A->off_S = A->off_E + (int64_t)H.E.size();
-    A->off_N = A->off_S + (int64_t)H.S.size();
-    A->off_VF = A->off_N + (int64_t)H.N.size();
+    A->off_E = A->off_V + (int64_t)T.n * k;
+    A->off_S = A->off_E + (int64_t)T.ncl * k * k;
+    A->off_N = A->off_S + (int64_t)BT.adm_list.size() * k * k;
+    A->off_VF = A->off_N + BT.near_total;
     A->off_W = A->off_V;
     A->off_F = A->off_E;
     A->off_WF = A->off_VF;
     A->arena_len = A->off_VF + (int64_t)(T.depth + 1) * T.n * k;
     if (cudaMalloc(&A->d_arena, A->arena_len * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
       delete A;
       return H2_ENOMEM;
     }
-    cudaMemcpy(A->d_arena + A->off_V, H.V.data(), H.V.size() * 8, cudaMemcpyHostToDevice);
-    cudaMemcpy(A->d_arena + A->off_E, H.E.data(), H.E.size() * 8, cudaMemcpyHostToDevice);
-    cudaMemcpy(A->d_arena + A->off_S, H.S.data(), H.S.size() * 8, cudaMemcpyHostToDevice);
-    cudaMemcpy(A->d_arena + A->off_N, H.N.data(), H.N.size() * 8, cudaMemcpyHostToDevice);
+    // E_0 (the root has no parent) stays zero
+    cudaMemsetAsync(A->d_arena + A->off_E, 0, (size_t)k * k * sizeof(double), g_stream);
+    std::string err;
+    rc = assemble_device(points, T, BT, o->order, o->kernel, o->kparam, A->d_arena + A->off_V,
+                         A->d_arena + A->off_E, A->d_arena + A->off_S, A->d_arena + A->off_N, g_stream, err);
+    if (rc) {
+      g_last_cuda = err;
+      h2_free(A);
+      return rc;
+    }
     std::vector<int> ints(2 * T.ncl + 1, k);
     ints[2 * T.ncl] = 0;
     cudaMalloc(&A->d_int, ints.size() * sizeof(int));
@@ -519,7 +594,6 @@ void h2_free(h2_matrix* A) {
     cudaEventSynchronize(A->done);
     cudaEventDestroy(A->done);
   }
-  A->plans.clear();
   if (A->d_arena) cudaFree(A->d_arena);
   if (A->d_int) cudaFree(A->d_int);
   delete A;
@@ -545,40 +619,38 @@ static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   int rc = lib_init();
   if (rc) return rc;
   if ((rc = ensure_level_bases(A, s)) || (rc = ensure_level_bases(B, s))) return rc;
-  // plan (cached in A)
-  std::shared_ptr<PlanRT> rt;
-  {
-    std::lock_guard<std::mutex> lk(A->mu);
-    auto key = std::make_pair((const h2_matrix*)B,
-                              (precision * 100 + max_rank) * 1000 + (int)std::lround(theta * 997.0));
-    auto it = A->plans.find(key);
-    if (it != A->plans.end() && it->second->uid_b == B->uid) {
-      rt = std::static_pointer_cast<PlanRT>(it->second->rt);
-    } else {
-      MulOptions mo;
-      mo.eta = A->eta;
-      mo.theta = theta;
-      mo.max_rank = max_rank;
-      mo.precision = precision;
-      std::shared_ptr<Plan> plan;
-      try {
-        plan = make_product_plan(desc_of(A), desc_of(B), mo);
-      } catch (const std::exception& ex) {
-        g_last_cuda = ex.what();
-        return H2_EINVAL;
-      }
+  // plan: shared by all operand pairs of the same structure
+  const PlanKey key{matrix_sig(A), matrix_sig(B),
+                    (precision * 100 + max_rank) * 1000 + (int)std::lround(theta * 997.0)};
+  std::shared_ptr<PlanRT> rt = plan_lookup(key);
+  if (!rt) {
+    MulOptions mo;
+    mo.eta = A->eta;
+    mo.theta = theta;
+    mo.max_rank = max_rank;
+    mo.precision = precision;
+    std::shared_ptr<Plan> plan;
+    try {
+      plan = make_product_plan(desc_of(A), desc_of(B), mo);
+    } catch (const std::exception& ex) {
+      g_last_cuda = ex.what();
+      return H2_EINVAL;
+    }
+    std::vector<int> rank_src;
+    rank_src.insert(rank_src.end(), plan->rank_row_slot.begin(), plan->rank_row_slot.end());
+    rank_src.insert(rank_src.end(), plan->rank_col_slot.begin(), plan->rank_col_slot.end());
+    rt = std::make_shared<PlanRT>();
+    rt->plan = plan;
+    rc = upload_plan(*rt, rank_src);
+    if (rc == H2_ENOMEM) {
+      // the cached plans hold device memory: release them and retry once
+      plan_cache_clear();
       rt = std::make_shared<PlanRT>();
       rt->plan = plan;
-      std::vector<int> rank_src;
-      rank_src.insert(rank_src.end(), plan->rank_row_slot.begin(), plan->rank_row_slot.end());
-      rank_src.insert(rank_src.end(), plan->rank_col_slot.begin(), plan->rank_col_slot.end());
       rc = upload_plan(*rt, rank_src);
-      if (rc) return rc;
-      auto entry = std::make_shared<PlanEntry>();
-      entry->rt = rt;
-      entry->uid_b = B->uid;
-      A->plans[key] = entry;
     }
+    if (rc) return rc;
+    plan_insert(key, rt);
   }
   Plan& P = *rt->plan;
   auto C = new h2_matrix();

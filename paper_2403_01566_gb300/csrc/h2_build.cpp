@@ -149,6 +149,14 @@ void build_block_tree(const Tree& R, const Tree& C, double eta, BlockTree& B) {
     B.child0[b] = c0;
     for (int i = 3; i >= 0; --i) stack.push_back(c0 + i);
   }
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  for (size_t b = 0; b < B.t.size(); ++b) {
+    mix((uint64_t)B.t[b]);
+    mix((uint64_t)B.s[b]);
+    mix((uint64_t)(B.adm[b] + 1));
+  }
+  B.sig = h;
 }
 
 // ------------------------------------------------------------ Chebyshev ----
@@ -158,12 +166,8 @@ struct Interp {
   double* nd(int c, int a) { return &nodes[((size_t)c * dim + a) * m]; }
 };
 
-static void make_interp(const Tree& T, int order, Interp& I) {
-  I.m = order;
-  I.dim = T.dim;
-  I.k = 1;
-  for (int a = 0; a < T.dim; ++a) I.k *= order;
-  I.nodes.assign((size_t)T.ncl * T.dim * order, 0.0);
+std::vector<double> chebyshev_nodes(const Tree& T, int order) {
+  std::vector<double> nodes((size_t)T.ncl * T.dim * order, 0.0);
   const double rootdiag = box_diam(T, 0);
   const double minw = rootdiag > 0.0 ? 1e-6 * rootdiag : 1e-6;
   const double pi = 3.14159265358979323846;
@@ -175,10 +179,19 @@ static void make_interp(const Tree& T, int order, Interp& I) {
         lo = mid - 0.5 * minw;
         hi = mid + 0.5 * minw;
       }
-      double* x = I.nd(c, a);
+      double* x = &nodes[((size_t)c * T.dim + a) * order];
       for (int nu = 0; nu < order; ++nu)
         x[nu] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * std::cos((2.0 * nu + 1.0) * pi / (2.0 * order));
     }
+  return nodes;
+}
+
+static void make_interp(const Tree& T, int order, Interp& I) {
+  I.m = order;
+  I.dim = T.dim;
+  I.k = 1;
+  for (int a = 0; a < T.dim; ++a) I.k *= order;
+  I.nodes = chebyshev_nodes(T, order);
 }
 
 // ell_{c,nu}(p) for one point p (dim coordinates) -> out[k]

@@ -24,4 +24,9 @@ double kernel_value(int kind, const double* kparam, const double* x, const doubl
 void assemble_chebyshev(const double* points, const Tree& T, const BlockTree& B, int order, int kind,
                         const double* kparam, HostH2& out);
 
+// First-kind Chebyshev points of every cluster box (ncl x dim x order, axes
+// narrower than 1e-6 of the root diagonal widened), shared by the host and the
+// device assembly.
+std::vector<double> chebyshev_nodes(const Tree& T, int order);
+
 }  // namespace h2

@@ -41,6 +41,7 @@ struct BlockTree {
   std::vector<int64_t> near_off;  // inadmissible leaf -> offset of its dense block
   int64_t near_total = 0;
   std::unordered_map<int64_t, int> index;   // key(t, s) -> block
+  uint64_t sig = 0;                         // structure hash of (t, s, adm) (FNV-1a)
   static int64_t key(int a, int b) { return ((int64_t)a << 32) | (uint32_t)b; }
   int find(int a, int b) const {
     auto it = index.find(key(a, b));
@@ -55,12 +56,6 @@ void build_block_tree(const Tree& rows, const Tree& cols, double eta, BlockTree&
 void build_cluster_tree(const double* points, int64_t n, int dim, int leaf_size, Tree& out);
 
 struct Plan;
-
-// A cached product plan (opaque runtime state) for one right factor.
-struct PlanEntry {
-  std::shared_ptr<void> rt;
-  uint64_t uid_b = 0;
-};
 
 }  // namespace h2
 
@@ -84,7 +79,6 @@ struct h2_matrix {
   cudaEvent_t done = nullptr;                // completion of the product that made it
   cudaStream_t stream = nullptr;
   std::mutex mu;
-  std::map<std::pair<const h2_matrix*, int>, std::shared_ptr<h2::PlanEntry>> plans;  // as left factor
   bool levels_ready = false;                 // explicit level bases computed
   uint64_t uid = 0;
 };

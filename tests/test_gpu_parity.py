@@ -163,3 +163,28 @@ def test_full_size_grid_against_oracle():
         assert np.linalg.norm(yg - yo) <= 1e-10 * np.linalg.norm(yo)
         yab = X.matvec(Y.matvec(x))
         assert np.linalg.norm(yg - yab) <= 1e-6 * np.sqrt(2 * 32) * np.linalg.norm(yab)
+
+
+def test_plan_shared_by_operands_of_the_same_structure():
+    """A cached plan serves every operand pair of the same structure: it holds
+    no numeric data.  A second left factor with another kernel (same points,
+    same trees, same block tree) reuses the plan of the first product and must
+    still reproduce its own oracle product."""
+    w = I.grid_2d(32)
+    A1, B = gpu_pair(w)
+    C1 = h2.mul(A1, B, 1e-6)
+    k2 = I.KernelSpec(I.KERNEL_EXP, 2.0, 0.5, 0.3)
+    A2 = h2.build(w.points, k2, w.eta, w.leaf_size, w.order)
+    C2 = h2.mul(A2, B, 1e-6)
+    X2 = O.build_h2(w.points, k2.kind, k2.kparam(), w.eta, w.leaf_size, w.order)
+    Y = O.build_h2(w.points, w.kernel_b.kind, w.kernel_b.kparam(), w.eta, w.leaf_size, w.order, tree=X2.rows)
+    res = O.multiply(X2, Y, 1e-6)
+    Z = X2.dense() @ Y.dense()
+    d_oracle, d_exact = blockrel(C2.to_dense(), res.C.dense(), Z, res.C.blocks)
+    assert d_oracle <= 1e-10, d_oracle
+    assert d_exact <= 1e-6, d_exact
+    # and the first product is untouched by the second
+    X1, Y1 = build_pair(w)
+    res1 = O.multiply(X1, Y1, 1e-6)
+    d1, _ = blockrel(C1.to_dense(), res1.C.dense(), X1.dense() @ Y1.dense(), res1.C.blocks)
+    assert d1 <= 1e-10, d1
