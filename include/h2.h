@@ -149,6 +149,22 @@ int h2_check(const h2_matrix* C);
  * pointers, else host pointers.  Runs on the library stream and synchronizes. */
 int h2_matvec(const h2_matrix* A, const double* x, double* y, int on_device);
 
+/* Y = A X for nrhs right-hand sides at once (Section 2: forward transform
+ * x^_s = W_s^* x|_s up the column tree, couplings y^_t = sum_s S_ts x^_s,
+ * backward transform down the row tree, leaf bases and nearfield), as
+ * level-wise batched GEMMs with nrhs columns.
+ *   X        n_cols x nrhs, column-major (vector j at X + j * n_cols), caller ordering
+ *   Y        n_rows x nrhs, column-major, caller ordering (written)
+ *   nrhs     1 .. 4096
+ *   on_device  1: X and Y are device pointers; 0: host pointers (staged through
+ *            the device; the call returns when Y is written)
+ *   stream   cudaStream_t for the work, or NULL for the library stream (device
+ *            pointers and a NULL stream: the call returns when Y is written;
+ *            with a stream it returns after enqueueing)
+ * Plans are cached per (matrix structure, nrhs).  Returns H2_EINVAL for null
+ * pointers or nrhs out of range. */
+int h2_matvec_batch(const h2_matrix* A, const double* X, double* Y, int nrhs, int on_device, void* stream);
+
 /* Dense n x n column-major expansion (caller ordering) into `out` (host or device). */
 int h2_to_dense(const h2_matrix* A, double* out, int on_device);
 

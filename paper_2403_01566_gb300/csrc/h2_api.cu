@@ -197,7 +197,8 @@ static int run_plan(PlanRT& rt, double* bx, double* by, double* bc, int* out_int
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaMemcpyAsync(rt.d_slot, rt.d_slot_init, sizeof(int) * P.slot_init.size(), cudaMemcpyDeviceToDevice, cs);
+    if (!P.slot_init.empty())
+      cudaMemcpyAsync(rt.d_slot, rt.d_slot_init, sizeof(int) * P.slot_init.size(), cudaMemcpyDeviceToDevice, cs);
     cudaMemsetAsync(rt.d_err, 0, sizeof(int), cs);
     for (const Stage& st : P.stages) launch_stage(st, rt.d_ctx, rt.dj, rt.svd_smem, cs);
     launch_finalize(rt.d_ctx, rt.nrank, cs);
@@ -467,6 +468,59 @@ static void plan_cache_clear() {
   }
 }
 
+// Batched matrix-vector products: plans per (matrix structure, nrhs), and the
+// permutations between the caller's ordering (column-major n x nrhs) and the
+// cluster ordering of the plan (row-major n x nrhs).
+constexpr int MV_MAXRHS = 4096;
+struct MvKey {
+  uint64_t sig;
+  int nrhs;
+  bool operator==(const MvKey& o) const { return sig == o.sig && nrhs == o.nrhs; }
+};
+constexpr size_t MV_CACHE_MAX = 4;
+std::mutex g_mv_mu;
+std::list<std::pair<MvKey, std::shared_ptr<PlanRT>>> g_mv;  // most recent first
+
+static std::shared_ptr<PlanRT> mv_lookup(const MvKey& k) {
+  std::lock_guard<std::mutex> lk(g_mv_mu);
+  for (auto it = g_mv.begin(); it != g_mv.end(); ++it)
+    if (it->first == k) {
+      g_mv.splice(g_mv.begin(), g_mv, it);
+      return g_mv.front().second;
+    }
+  return nullptr;
+}
+
+static void mv_insert(const MvKey& k, std::shared_ptr<PlanRT> rt) {
+  std::shared_ptr<PlanRT> evicted;
+  std::lock_guard<std::mutex> lk(g_mv_mu);
+  g_mv.emplace_front(k, std::move(rt));
+  if (g_mv.size() > MV_CACHE_MAX) {
+    evicted = std::move(g_mv.back().second);
+    g_mv.pop_back();
+  }
+}
+
+// Xc[r * nrhs + j] = X[j * n + perm[r]]
+__global__ void k_perm_gather(const double* __restrict__ X, const int* __restrict__ perm, int64_t n, int nrhs,
+                              double* __restrict__ Xc) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / nrhs;
+    const int j = (int)(e % nrhs);
+    Xc[e] = X[(int64_t)j * n + perm[r]];
+  }
+}
+
+// Y[j * n + perm[r]] = Yc[r * nrhs + j]
+__global__ void k_perm_scatter(const double* __restrict__ Yc, const int* __restrict__ perm, int64_t n, int nrhs,
+                               double* __restrict__ Y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / nrhs;
+    const int j = (int)(e % nrhs);
+    Y[(int64_t)j * n + perm[r]] = Yc[e];
+  }
+}
+
 static int ensure_level_bases(h2_matrix* A, cudaStream_t s) {
   if (A->levels_ready) return H2_OK;
   const double params[PARAM_COUNT] = {0.0, 0.0};
@@ -596,6 +650,7 @@ void h2_free(h2_matrix* A) {
   }
   if (A->d_arena) cudaFree(A->d_arena);
   if (A->d_int) cudaFree(A->d_int);
+  if (A->d_perm) cudaFree(A->d_perm);
   delete A;
 }
 
@@ -765,33 +820,66 @@ int h2_info(const h2_matrix* A, h2_stats* st) {
 }
 
 int h2_matvec(const h2_matrix* Ac, const double* x, double* y, int on_device) {
-  if (!Ac || !x || !y) return H2_EINVAL;
+  return h2_matvec_batch(Ac, x, y, 1, on_device, nullptr);
+}
+
+int h2_matvec_batch(const h2_matrix* Ac, const double* X, double* Y, int nrhs, int on_device, void* stream) {
+  if (!Ac || !X || !Y || nrhs <= 0 || nrhs > MV_MAXRHS) return H2_EINVAL;
   h2_matrix* A = const_cast<h2_matrix*>(Ac);
   int rc = lib_init();
   if (rc) return rc;
-  if (A->done) CK(cudaEventSynchronize(A->done));
-  cudaStream_t s = g_stream;
-  PlanRT rt;
-  rt.plan = make_matvec_plan(desc_of(A));
-  rc = upload_plan(rt, {});
-  if (rc) return rc;
-  const int nr = A->rows->n, nc = A->cols->n;
-  std::vector<double> xc(nc), yc(nr), xh(nc);
-  if (on_device) CK(cudaMemcpy(xh.data(), x, nc * 8, cudaMemcpyDeviceToHost));
-  else std::memcpy(xh.data(), x, nc * 8);
-  for (int i = 0; i < nc; ++i) xc[i] = xh[A->cols->perm[i]];
-  CK(cudaMemcpy(rt.d_ws, xc.data(), nc * 8, cudaMemcpyHostToDevice));
+  cudaStream_t s = stream ? (cudaStream_t)stream : g_stream;
+  if (A->done) CK(cudaStreamWaitEvent(s, A->done, 0));
+  const int64_t nr = A->rows->n, nc = A->cols->n;
+  if (!A->d_perm) {
+    std::vector<int> p(nr + nc);
+    for (int64_t i = 0; i < nr; ++i) p[i] = (int)A->rows->perm[i];
+    for (int64_t i = 0; i < nc; ++i) p[nr + i] = (int)A->cols->perm[i];
+    CK(cudaMalloc(&A->d_perm, p.size() * sizeof(int)));
+    CK(cudaMemcpy(A->d_perm, p.data(), p.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  const MvKey key{matrix_sig(A), nrhs};
+  std::shared_ptr<PlanRT> rt = mv_lookup(key);
+  if (!rt) {
+    rt = std::make_shared<PlanRT>();
+    rt->plan = make_matvec_plan(desc_of(A), nrhs);
+    if ((rc = upload_plan(*rt, {}))) return rc;
+    mv_insert(key, rt);
+  }
+  const Plan& P = *rt->plan;
+  // the plan's workspace is shared by its replays: order this call after the last
+  CK(cudaStreamWaitEvent(s, rt->last, 0));
+  double* Xc = rt->d_ws + P.mv_ox;
+  double* Yc = rt->d_ws + P.mv_oy;
+  const double* Xd = X;
+  double* Yd = Y;
+  double* stage = nullptr;
+  if (!on_device) {  // caller arrays on the host: stage them on the device
+    CK(cudaMallocAsync(&stage, (size_t)(nr + nc) * nrhs * sizeof(double), s));
+    CK(cudaMemcpyAsync(stage, X, (size_t)nc * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+    Xd = stage;
+    Yd = stage + (size_t)nc * nrhs;
+  }
+  const int64_t nx = nc * nrhs, ny = nr * nrhs;
+  k_perm_gather<<<(unsigned)std::min<int64_t>((nx + 255) / 256, 65535 * 8), 256, 0, s>>>(Xd, A->d_perm + nr, nc,
+                                                                                         nrhs, Xc);
   const double params[PARAM_COUNT] = {0.0, 0.0};
-  rc = run_plan(rt, A->d_arena, nullptr, nullptr, nullptr, params, s, false);
-  if (rc) return rc;
-  CK(cudaStreamSynchronize(s));
-  // y lies after x in the workspace (offset rounded to 32 doubles)
-  const int64_t oy = ((int64_t)std::max(nc, 1) + 31) & ~int64_t(31);
-  CK(cudaMemcpy(yc.data(), rt.d_ws + oy, nr * 8, cudaMemcpyDeviceToHost));
-  std::vector<double> yo(nr);
-  for (int i = 0; i < nr; ++i) yo[A->rows->perm[i]] = yc[i];
-  if (on_device) CK(cudaMemcpy(y, yo.data(), nr * 8, cudaMemcpyHostToDevice));
-  else std::memcpy(y, yo.data(), nr * 8);
+  rc = run_plan(*rt, A->d_arena, nullptr, nullptr, nullptr, params, s, true);
+  if (rc) {
+    if (stage) cudaFreeAsync(stage, s);
+    return rc;
+  }
+  k_perm_scatter<<<(unsigned)std::min<int64_t>((ny + 255) / 256, 65535 * 8), 256, 0, s>>>(Yc, A->d_perm, nr, nrhs,
+                                                                                          Yd);
+  CK(cudaEventRecord(rt->last, s));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(Y, Yd, (size_t)nr * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaFreeAsync(stage, s));
+    CK(cudaStreamSynchronize(s));
+  } else if (!stream) {
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaGetLastError());
   return H2_OK;
 }
 

@@ -72,6 +72,7 @@ struct h2_matrix {
   int64_t off_V = 0, off_E = 0, off_W = 0, off_F = 0, off_S = 0, off_N = 0;
   int64_t off_VF = -1, off_WF = -1;          // explicit level bases (depth+1) x n x kpad
   int* d_int = nullptr;                      // [rank_row ncl][rank_col ncl][err 1]
+  int* d_perm = nullptr;                     // [rows perm n][cols perm n], made on first use
   bool same_basis = false;                   // W == V, F == E (Nystroem builds)
   int nagglomerated = 0;
   int launches = 0;

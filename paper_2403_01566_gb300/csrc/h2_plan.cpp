@@ -1533,61 +1533,74 @@ std::shared_ptr<Plan> make_levelbasis_plan(const Tree& T, int k, int ar, int64_t
   return plan;
 }
 
-std::shared_ptr<Plan> make_matvec_plan(const MatDesc& A) {
+std::shared_ptr<Plan> make_matvec_plan(const MatDesc& A, int nrhs) {
   auto plan = std::make_shared<Plan>();
   Builder B(*plan);
   const Tree& R = *A.rows;
   const Tree& C = *A.cols;
   const BlockTree& BT = *A.blocks;
   const int k = A.k, D = C.depth;
-  const int64_t ox = B.alloc(C.n), oy = B.alloc(R.n);
-  const int64_t oxh = B.alloc((int64_t)C.ncl * k), oyh = B.alloc((int64_t)R.ncl * k);
+  const int64_t q = nrhs;  // every vector block is row-major with nrhs columns
+  const int64_t ox = B.alloc(C.n * q), oy = B.alloc(R.n * q);
+  const int64_t oxh = B.alloc((int64_t)C.ncl * k * q), oyh = B.alloc((int64_t)R.ncl * k * q);
+  plan->mv_ox = ox;
+  plan->mv_oy = oy;
+  // right-hand-side columns in tiles of GEMM_MAXTILE
+  auto cols = [&](const std::function<void(int, Dim)>& emit) {
+    for (int c0 = 0; c0 < nrhs; c0 += GEMM_MAXTILE) emit(c0, DC(std::min(GEMM_MAXTILE, nrhs - c0)));
+  };
   // forward transform x^_s = W_s^* x|_s
-  for (int s = Tree::first(D); s < C.ncl; ++s) {
-    B.out(PT(AR_WS, oxh + (int64_t)s * k), 1, DC(k), DC(1), 0);
-    B.term2(mref(PT(AR_X, A.off_W + (int64_t)C.off[s] * k), k, 1), mref(PT(AR_WS, ox + C.off[s]), 1), DC(C.size[s]));
-  }
+  for (int s = Tree::first(D); s < C.ncl; ++s)
+    cols([&](int c0, Dim w) {
+      B.out(PT(AR_WS, oxh + (int64_t)s * k * q + c0), q, DC(k), w, 0);
+      B.term2(mref(PT(AR_X, A.off_W + (int64_t)C.off[s] * k), k, 1), mref(PT(AR_WS, ox + C.off[s] * q + c0), q),
+              DC(C.size[s]));
+    });
   B.flush_gemm(0);
   for (int l = D - 1; l >= 0; --l) {
-    for (int s = Tree::first(l); s < Tree::first(l + 1); ++s) {
-      B.out(PT(AR_WS, oxh + (int64_t)s * k), 1, DC(k), DC(1), 0);
-      for (int i = 0; i < 2; ++i) {
-        const int c = Tree::child(s, i);
-        B.term2(mref(PT(AR_X, A.off_F + (int64_t)c * k * k), k, 1), mref(PT(AR_WS, oxh + (int64_t)c * k), 1), DC(k));
-      }
-    }
+    for (int s = Tree::first(l); s < Tree::first(l + 1); ++s)
+      cols([&](int c0, Dim w) {
+        B.out(PT(AR_WS, oxh + (int64_t)s * k * q + c0), q, DC(k), w, 0);
+        for (int i = 0; i < 2; ++i) {
+          const int c = Tree::child(s, i);
+          B.term2(mref(PT(AR_X, A.off_F + (int64_t)c * k * k), k, 1), mref(PT(AR_WS, oxh + (int64_t)c * k * q + c0), q),
+                  DC(k));
+        }
+      });
     B.flush_gemm(0);
   }
   // coupling y^_t = sum_s S_ts x^_s
   std::vector<std::vector<int>> byrow(R.ncl);
   for (int b : BT.adm_list) byrow[BT.t[b]].push_back(b);
-  for (int t = 0; t < R.ncl; ++t) {
-    B.out(PT(AR_WS, oyh + (int64_t)t * k), 1, DC(k), DC(1), 0);
-    for (int b : byrow[t])
-      B.term2(mref(PT(AR_X, A.off_S + (int64_t)BT.leafidx[b] * k * k), k),
-              mref(PT(AR_WS, oxh + (int64_t)BT.s[b] * k), 1), DC(k));
-  }
+  for (int t = 0; t < R.ncl; ++t)
+    cols([&](int c0, Dim w) {
+      B.out(PT(AR_WS, oyh + (int64_t)t * k * q + c0), q, DC(k), w, 0);
+      for (int b : byrow[t])
+        B.term2(mref(PT(AR_X, A.off_S + (int64_t)BT.leafidx[b] * k * k), k),
+                mref(PT(AR_WS, oxh + (int64_t)BT.s[b] * k * q + c0), q), DC(k));
+    });
   B.flush_gemm(0);
   // backward transform y^_c += E_c y^_parent
   for (int l = 1; l <= D; ++l) {
-    for (int c = Tree::first(l); c < Tree::first(l + 1); ++c) {
-      B.out(PT(AR_WS, oyh + (int64_t)c * k), 1, DC(k), DC(1), 1);
-      B.term2(mref(PT(AR_X, A.off_E + (int64_t)c * k * k), k), mref(PT(AR_WS, oyh + (int64_t)Tree::parent(c) * k), 1),
-              DC(k));
-    }
+    for (int c = Tree::first(l); c < Tree::first(l + 1); ++c)
+      cols([&](int c0, Dim w) {
+        B.out(PT(AR_WS, oyh + (int64_t)c * k * q + c0), q, DC(k), w, 1);
+        B.term2(mref(PT(AR_X, A.off_E + (int64_t)c * k * k), k),
+                mref(PT(AR_WS, oyh + (int64_t)Tree::parent(c) * k * q + c0), q), DC(k));
+      });
     B.flush_gemm(0);
   }
   // leaves: y|_t = V_t y^_t + sum_s N_ts x|_s
   std::vector<std::vector<int>> nrow(R.ncl);
   for (int b : BT.inadm_list) nrow[BT.t[b]].push_back(b);
   for (int t = Tree::first(D); t < R.ncl; ++t) {
-    B.tiles(PT(AR_WS, oy + R.off[t]), 1, R.size[t], dv(1), 0, [&](int r0, int, int, Dim) {
-      B.term2(mref(PT(AR_X, A.off_V + (int64_t)(R.off[t] + r0) * k), k), mref(PT(AR_WS, oyh + (int64_t)t * k), 1),
-              DC(k));
+    B.tiles(PT(AR_WS, oy + R.off[t] * q), q, R.size[t], dv(nrhs), 0, [&](int r0, int, int c0, Dim) {
+      B.term2(mref(PT(AR_X, A.off_V + (int64_t)(R.off[t] + r0) * k), k),
+              mref(PT(AR_WS, oyh + (int64_t)t * k * q + c0), q), DC(k));
       for (int b : nrow[t]) {
         const int s = BT.s[b];
         B.term2(mref(PT(AR_X, A.off_N + BT.near_off[BT.leafidx[b]] + (int64_t)r0 * C.size[s]), C.size[s]),
-                mref(PT(AR_WS, ox + C.off[s]), 1), DC(C.size[s]));
+                mref(PT(AR_WS, ox + C.off[s] * q + c0), q), DC(C.size[s]));
       }
     });
   }

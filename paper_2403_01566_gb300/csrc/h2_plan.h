@@ -50,6 +50,7 @@ struct Plan {
   std::vector<double> konst;     // AR_K contents
   int64_t ws_len = 0;            // doubles
   int64_t fac_len = 0;           // doubles of the terminal-factor arena (placed after the workspace)
+  int64_t mv_ox = 0, mv_oy = 0;  // matrix-vector plans: X and Y in the workspace
   int nscal = PARAM_COUNT;       // scal/nrm entries (first PARAM_COUNT are parameters)
   int svd_maxrows = 1, svd_maxcols = 1;
   // product layout (valid for product plans)
@@ -75,8 +76,9 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
 std::shared_ptr<Plan> make_levelbasis_plan(const Tree& T, int k, int ar, int64_t off_leaf,
                                            int64_t off_trans, int64_t off_out);
 
-// y = A x with x (cluster order) at ws[0..n) and y at ws[n..2n).
-std::shared_ptr<Plan> make_matvec_plan(const MatDesc& A);
+// Y = A X for nrhs right-hand sides: X (cluster order, row-major n x nrhs)
+// at ws[mv_ox..), Y likewise at ws[mv_oy..).
+std::shared_ptr<Plan> make_matvec_plan(const MatDesc& A, int nrhs = 1);
 
 // Dense expansion in cluster order (row-major n_rows x n_cols) at ws[0..).
 std::shared_ptr<Plan> make_dense_plan(const MatDesc& A);

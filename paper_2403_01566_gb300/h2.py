@@ -65,6 +65,7 @@ def _lib():
         lib.h2_check.argtypes = [vp]
         lib.h2_mul_profile.argtypes = [vp, vp, C.c_double, C.POINTER(MulOpts), C.POINTER(KernelProf), C.POINTER(vp)]
         lib.h2_matvec.argtypes = [vp, vp, vp, C.c_int]
+        lib.h2_matvec_batch.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         lib.h2_to_dense.argtypes = [vp, vp, C.c_int]
         lib.h2_info.argtypes = [vp, C.POINTER(Stats)]
         lib.h2_ranks.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -135,6 +136,26 @@ class H2Matrix:
         _check(_lib().h2_matvec(self._h, x.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p), 0),
                "h2_matvec")
         return y
+
+    def matvec_batch(self, X, stream=None):
+        """Y = A X for the columns of X (n x nrhs): a host numpy array, or a CUDA
+        torch tensor (then Y is a CUDA tensor; the columns must be contiguous,
+        i.e. X.T contiguous)."""
+        if hasattr(X, "is_cuda") and X.is_cuda:
+            import torch
+            n, nrhs = X.shape
+            Xt = X.t().contiguous()  # column-major n x nrhs
+            Yt = torch.empty((nrhs, self.info().n), dtype=torch.float64, device=X.device)
+            _check(_lib().h2_matvec_batch(self._h, C.c_void_p(Xt.data_ptr()), C.c_void_p(Yt.data_ptr()), nrhs, 1,
+                                          C.c_void_p(stream) if stream else None), "h2_matvec_batch")
+            return Yt.t()
+        X = np.asarray(X, dtype=np.float64)
+        n, nrhs = X.shape
+        Xf = np.asfortranarray(X)
+        Y = np.empty((self.info().n, nrhs), dtype=np.float64, order="F")
+        _check(_lib().h2_matvec_batch(self._h, Xf.ctypes.data_as(C.c_void_p), Y.ctypes.data_as(C.c_void_p), nrhs, 0,
+                                      None), "h2_matvec_batch")
+        return np.ascontiguousarray(Y)
 
     def to_dense(self):
         st = self.info()
