@@ -165,6 +165,29 @@ int h2_matvec(const h2_matrix* A, const double* x, double* y, int on_device);
  * pointers or nrhs out of range. */
 int h2_matvec_batch(const h2_matrix* A, const double* X, double* Y, int nrhs, int on_device, void* stream);
 
+/* ---- H-matrix output variant -------------------------------------------
+ * C ~ A*B as a standard H-matrix (Section 5.1): the product is accumulated
+ * and, where the induced block structure is finer than the target block tree,
+ * agglomerated with the coarsening error control (eps_c = eps/3 per block),
+ * exactly as in h2_mul; the nested-basis recompression (Sections 5.2-5.3) is
+ * skipped.  Every admissible block keeps its own low-rank factors
+ * C_b = L_b R_b^T (accumulated blocks rank 2k, agglomerated blocks the
+ * truncated rank); inadmissible leaves are dense.  Same operands, options and
+ * errors as h2_mul (opts->precision must be 0). */
+typedef struct h2_hmatrix h2_hmatrix;
+int h2_mul_h(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts, h2_hmatrix** C);
+
+/* Dense n_rows x n_cols column-major expansion (caller ordering) into `out`
+ * (host, or device when on_device = 1). */
+int h2_hmatrix_to_dense(const h2_hmatrix* C, double* out, int on_device);
+
+/* Ranks of the admissible blocks in block-tree leaf order (`ranks` holds
+ * nadm ints); nadm, the largest rank and the device bytes are optional
+ * outputs (NULL to skip). */
+int h2_hmatrix_ranks(const h2_hmatrix* C, int* ranks, int* nadm, int* rank_max, int64_t* device_bytes);
+
+void h2_hmatrix_free(h2_hmatrix* C);
+
 /* Dense n x n column-major expansion (caller ordering) into `out` (host or device). */
 int h2_to_dense(const h2_matrix* A, double* out, int on_device);
 

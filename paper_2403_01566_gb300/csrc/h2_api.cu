@@ -550,6 +550,18 @@ static int ensure_level_bases(h2_matrix* A, cudaStream_t s) {
 
 using namespace h2;
 
+// The opaque H-matrix product handle.
+struct h2_hmatrix {
+  std::shared_ptr<h2::Tree> rows, cols;
+  std::shared_ptr<h2::BlockTree> blocks;
+  double* d_arena = nullptr;
+  int64_t arena_len = 0, off_N = 0;
+  std::vector<int64_t> off_L, off_R;
+  std::vector<int> w;
+  int* d_int = nullptr;  // [rank of each admissible leaf][err]
+  cudaEvent_t done = nullptr;
+};
+
 extern "C" {
 
 const char* h2_strerror(int code) {
@@ -654,6 +666,9 @@ void h2_free(h2_matrix* A) {
   delete A;
 }
 
+static int hmul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts,
+                     h2_hmatrix** Cout);
+
 static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts, h2_kernel_prof* prof,
                     h2_matrix** Cout) {
   if (!Cout) return H2_EINVAL;
@@ -757,8 +772,143 @@ static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   return H2_OK;
 }
 
+static int hmul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts,
+                     h2_hmatrix** Cout) {
+  if (!Cout) return H2_EINVAL;
+  *Cout = nullptr;
+  if (!Ac || !Bc || !(eps >= 0.0) || !std::isfinite(eps)) return H2_EINVAL;
+  h2_matrix* A = const_cast<h2_matrix*>(Ac);
+  h2_matrix* B = const_cast<h2_matrix*>(Bc);
+  if (A->cols->hash != B->rows->hash || A->cols->n != B->rows->n) return H2_ETREE;
+  if (A->kpad != B->kpad) return H2_EINVAL;
+  if (opts && opts->precision != 0) return H2_EINVAL;
+  const int max_rank = opts ? opts->max_rank : 0;
+  if (max_rank < 0 || max_rank > GEMM_MAXTILE) return H2_EINVAL;
+  const bool sync = opts ? opts->sync != 0 : true;
+  cudaStream_t s = (opts && opts->stream) ? (cudaStream_t)opts->stream : g_stream;
+  int rc = lib_init();
+  if (rc) return rc;
+  if ((rc = ensure_level_bases(A, s)) || (rc = ensure_level_bases(B, s))) return rc;
+  const PlanKey key{matrix_sig(A), matrix_sig(B), -1 - max_rank};  // H-matrix plans: negative option codes
+  std::shared_ptr<PlanRT> rt = plan_lookup(key);
+  if (!rt) {
+    MulOptions mo;
+    mo.eta = A->eta;
+    mo.max_rank = max_rank;
+    mo.hmatrix = true;
+    std::shared_ptr<Plan> plan;
+    try {
+      plan = make_product_plan(desc_of(A), desc_of(B), mo);
+    } catch (const std::exception& ex) {
+      g_last_cuda = ex.what();
+      return H2_EINVAL;
+    }
+    rt = std::make_shared<PlanRT>();
+    rt->plan = plan;
+    rc = upload_plan(*rt, plan->rank_row_slot);
+    if (rc == H2_ENOMEM) {
+      plan_cache_clear();
+      rt = std::make_shared<PlanRT>();
+      rt->plan = plan;
+      rc = upload_plan(*rt, plan->rank_row_slot);
+    }
+    if (rc) return rc;
+    plan_insert(key, rt);
+  }
+  const Plan& P = *rt->plan;
+  auto C = new h2_hmatrix();
+  C->rows = A->rows;
+  C->cols = B->cols;
+  C->blocks = P.cblocks;
+  C->arena_len = P.c_len;
+  C->off_N = P.c_off_N;
+  C->off_L = P.hm_off_L;
+  C->off_R = P.hm_off_R;
+  C->w = P.hm_w;
+  const size_t nint = P.hm_off_L.size() + 1;
+  if (cudaMallocAsync(&C->d_arena, std::max<int64_t>(C->arena_len, 1) * sizeof(double), s) != cudaSuccess ||
+      cudaMallocAsync(&C->d_int, nint * sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    h2_hmatrix_free(C);
+    return H2_ENOMEM;
+  }
+  cudaMemsetAsync(C->d_arena, 0, C->arena_len * sizeof(double), s);
+  cudaMemsetAsync(C->d_int, 0, nint * sizeof(int), s);
+  const double params[PARAM_COUNT] = {0.0, eps / 3.0};
+  rc = run_plan(*rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, true);
+  if (rc) {
+    h2_hmatrix_free(C);
+    return rc;
+  }
+  cudaEventCreateWithFlags(&C->done, cudaEventDisableTiming);
+  cudaEventRecord(C->done, s);
+  *Cout = C;
+  if (sync) {
+    rc = h2_hmatrix_ranks(C, nullptr, nullptr, nullptr, nullptr);
+    if (rc) {
+      h2_hmatrix_free(C);
+      *Cout = nullptr;
+      return rc;
+    }
+  }
+  return H2_OK;
+}
+
 int h2_mul(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts, h2_matrix** C) {
   return mul_impl(A, B, eps, opts, nullptr, C);
+}
+
+int h2_mul_h(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts, h2_hmatrix** C) {
+  return hmul_impl(A, B, eps, opts, C);
+}
+
+void h2_hmatrix_free(h2_hmatrix* C) {
+  if (!C) return;
+  if (C->done) {
+    cudaEventSynchronize(C->done);
+    cudaEventDestroy(C->done);
+  }
+  if (C->d_arena) cudaFree(C->d_arena);
+  if (C->d_int) cudaFree(C->d_int);
+  delete C;
+}
+
+int h2_hmatrix_ranks(const h2_hmatrix* C, int* ranks, int* nadm, int* rank_max, int64_t* device_bytes) {
+  if (!C) return H2_EINVAL;
+  if (C->done) CK(cudaEventSynchronize(C->done));
+  const int na = (int)C->off_L.size();
+  std::vector<int> r(na + 1);
+  CK(cudaMemcpy(r.data(), C->d_int, (na + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  if (r[na] != 0) return map_err(r[na]);
+  if (ranks) std::copy(r.begin(), r.begin() + na, ranks);
+  if (nadm) *nadm = na;
+  if (rank_max) *rank_max = na ? *std::max_element(r.begin(), r.begin() + na) : 0;
+  if (device_bytes) *device_bytes = C->arena_len * 8 + (na + 1) * 4;
+  return H2_OK;
+}
+
+int h2_hmatrix_to_dense(const h2_hmatrix* C, double* out, int on_device) {
+  if (!C || !out) return H2_EINVAL;
+  int rc = lib_init();
+  if (rc) return rc;
+  if (C->done) CK(cudaEventSynchronize(C->done));
+  cudaStream_t s = g_stream;
+  PlanRT rt;
+  rt.plan = make_hmatrix_dense_plan(*C->rows, *C->cols, *C->blocks, C->off_N, C->off_L, C->off_R, C->w);
+  rc = upload_plan(rt, {});
+  if (rc) return rc;
+  const double params[PARAM_COUNT] = {0.0, 0.0};
+  rc = run_plan(rt, C->d_arena, nullptr, nullptr, nullptr, params, s, false);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  const int64_t nr = C->rows->n, nc = C->cols->n;
+  std::vector<double> d((size_t)nr * nc), o((size_t)nr * nc);
+  CK(cudaMemcpy(d.data(), rt.d_ws, d.size() * 8, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < nr; ++i)
+    for (int64_t j = 0; j < nc; ++j) o[(size_t)C->cols->perm[j] * nr + C->rows->perm[i]] = d[(size_t)i * nc + j];
+  if (on_device) CK(cudaMemcpy(out, o.data(), o.size() * 8, cudaMemcpyHostToDevice));
+  else std::memcpy(out, o.data(), o.size() * 8);
+  return H2_OK;
 }
 
 int h2_mul_profile(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts,

@@ -1215,6 +1215,34 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   }
   std::vector<int> fin_of_cb(BC.t.size(), -1);
   for (size_t i = 0; i < fin.size(); ++i) fin_of_cb[fin[i].cb] = (int)i;
+  if (opt.hmatrix) {
+    // H-matrix output: every admissible target leaf keeps its accumulated or
+    // agglomerated factors (the standard H-matrix approximation the product
+    // reaches before the nested-basis recompression); the nearfield is in
+    // place already
+    P.rank_row_slot.clear();
+    P.rank_col_slot.clear();
+    for (int cb : BC.adm_list) {
+      const int i = fin_of_cb[cb];
+      if (i < 0) throw std::runtime_error("admissible leaf without factors");
+      const Final& F = fin[i];
+      const int w = F.f.m.max;
+      const int64_t oL = P.c_len, oR = oL + (int64_t)F.f.rows_t * w;
+      P.c_len = oR + (int64_t)F.f.rows_r * w;
+      B.copy(F.f.L.p, F.f.L.ld, PT(AR_C, oL), w, DC(F.f.rows_t), F.f.m.d(), 0, 1.0, -1, DC(F.f.rows_t), DC(w));
+      B.copy(F.f.R.p, F.f.R.ld, PT(AR_C, oR), w, DC(F.f.rows_r), F.f.m.d(), 0, 1.0, -1, DC(F.f.rows_r), DC(w));
+      P.hm_off_L.push_back(oL);
+      P.hm_off_R.push_back(oR);
+      P.hm_w.push_back(w);
+      P.rank_row_slot.push_back(F.f.m.s >= 0 ? F.f.m.s : B.slot(F.f.m.c));
+    }
+    B.flush_copy(TAG_COUPLE);
+    P.ws_len = B.ws_peak;
+    P.fac_len = B.fac;
+    P.stats["final_adm"] = fin.size();
+    P.stats["stages"] = P.stages.size();
+    return plan;
+  }
   {
     const int64_t mark = B.ws;
     std::vector<std::array<int64_t, 4>> scr(fin.size());
@@ -1605,6 +1633,32 @@ std::shared_ptr<Plan> make_matvec_plan(const MatDesc& A, int nrhs) {
     });
   }
   B.flush_gemm(0);
+  plan->ws_len = B.ws_peak;
+  return plan;
+}
+
+std::shared_ptr<Plan> make_hmatrix_dense_plan(const Tree& R, const Tree& C, const BlockTree& BT, int64_t off_N,
+                                              const std::vector<int64_t>& off_L, const std::vector<int64_t>& off_R,
+                                              const std::vector<int>& w) {
+  auto plan = std::make_shared<Plan>();
+  Builder B(*plan);
+  const int64_t ld = C.n;
+  const int64_t od = B.alloc((int64_t)R.n * C.n);
+  for (size_t a = 0; a < BT.adm_list.size(); ++a) {
+    const int b = BT.adm_list[a], t = BT.t[b], s = BT.s[b];
+    B.tiles(PT(AR_WS, od + (int64_t)R.off[t] * ld + C.off[s]), ld, R.size[t], dv(C.size[s]), 0,
+            [&](int r0, int, int c0, Dim) {
+              B.term2(mref(PT(AR_X, off_L[a] + (int64_t)r0 * w[a]), w[a]),
+                      mref(PT(AR_X, off_R[a] + (int64_t)c0 * w[a]), w[a], 1), DC(w[a]));
+            });
+  }
+  B.flush_gemm(0);
+  for (size_t a = 0; a < BT.inadm_list.size(); ++a) {
+    const int b = BT.inadm_list[a], t = BT.t[b], s = BT.s[b];
+    B.copy(PT(AR_X, off_N + BT.near_off[a]), C.size[s], PT(AR_WS, od + (int64_t)R.off[t] * ld + C.off[s]), ld,
+           DC(R.size[t]), DC(C.size[s]), 0);
+  }
+  B.flush_copy(0);
   plan->ws_len = B.ws_peak;
   return plan;
 }

@@ -30,6 +30,7 @@ struct MulOptions {
   double theta = 0.25;   // weight factor (Section 5.3)
   int max_rank = 0;      // cap of the adaptive ranks (storage padding of C)
   int precision = 0;     // 0 FP64 throughout; 1 FP32 contractions (accumulation and couplings)
+  bool hmatrix = false;  // H-matrix output: stop after agglomeration (no nested-basis recompression)
 };
 
 // Indices into the per-product parameter block (ExecCtx::scal[0..]).
@@ -51,6 +52,12 @@ struct Plan {
   int64_t ws_len = 0;            // doubles
   int64_t fac_len = 0;           // doubles of the terminal-factor arena (placed after the workspace)
   int64_t mv_ox = 0, mv_oy = 0;  // matrix-vector plans: X and Y in the workspace
+  // H-matrix output (MulOptions::hmatrix): per admissible leaf of the target
+  // block tree (adm_list order) the factors L (|t| x w) and R (|r| x w) in the
+  // product arena, zero-padded to the width cap w; their ranks go to the
+  // product's integer array through rank_row_slot
+  std::vector<int64_t> hm_off_L, hm_off_R;
+  std::vector<int> hm_w;
   int nscal = PARAM_COUNT;       // scal/nrm entries (first PARAM_COUNT are parameters)
   int svd_maxrows = 1, svd_maxcols = 1;
   // product layout (valid for product plans)
@@ -82,5 +89,12 @@ std::shared_ptr<Plan> make_matvec_plan(const MatDesc& A, int nrhs = 1);
 
 // Dense expansion in cluster order (row-major n_rows x n_cols) at ws[0..).
 std::shared_ptr<Plan> make_dense_plan(const MatDesc& A);
+
+// Dense expansion (cluster order, row-major, at ws[0..)) of an H-matrix
+// product whose arena (AR_X) holds the nearfield at off_N (near_off layout)
+// and the admissible factors at off_L / off_R (width w, row-major).
+std::shared_ptr<Plan> make_hmatrix_dense_plan(const Tree& rows, const Tree& cols, const BlockTree& blocks,
+                                              int64_t off_N, const std::vector<int64_t>& off_L,
+                                              const std::vector<int64_t>& off_R, const std::vector<int>& w);
 
 }  // namespace h2

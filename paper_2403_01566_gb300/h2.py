@@ -66,6 +66,12 @@ def _lib():
         lib.h2_mul_profile.argtypes = [vp, vp, C.c_double, C.POINTER(MulOpts), C.POINTER(KernelProf), C.POINTER(vp)]
         lib.h2_matvec.argtypes = [vp, vp, vp, C.c_int]
         lib.h2_matvec_batch.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
+        lib.h2_mul_h.argtypes = [vp, vp, C.c_double, C.POINTER(MulOpts), C.POINTER(vp)]
+        lib.h2_hmatrix_to_dense.argtypes = [vp, vp, C.c_int]
+        lib.h2_hmatrix_ranks.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int64)]
+        lib.h2_hmatrix_free.argtypes = [vp]
+        lib.h2_hmatrix_free.restype = None
         lib.h2_to_dense.argtypes = [vp, vp, C.c_int]
         lib.h2_info.argtypes = [vp, C.POINTER(Stats)]
         lib.h2_ranks.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -189,6 +195,58 @@ def mul(A: H2Matrix, B: H2Matrix, eps: float, max_rank: int = 0, theta: float = 
     h = C.c_void_p()
     _check(_lib().h2_mul(A.handle, B.handle, float(eps), C.byref(o), C.byref(h)), "h2_mul")
     return H2Matrix(h.value)
+
+
+class HMatrix:
+    """An H-matrix product (h2_mul_h): low-rank factors per admissible block,
+    dense inadmissible leaves."""
+
+    def __init__(self, handle, n_rows, n_cols):
+        self._h = handle
+        self.shape = (n_rows, n_cols)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def ranks(self):
+        na, rmax, nb = C.c_int(), C.c_int(), C.c_int64()
+        _check(_lib().h2_hmatrix_ranks(self._h, None, C.byref(na), C.byref(rmax), C.byref(nb)), "h2_hmatrix_ranks")
+        r = np.empty(na.value, dtype=np.int32)
+        _check(_lib().h2_hmatrix_ranks(self._h, r.ctypes.data_as(C.POINTER(C.c_int)), None, None, None),
+               "h2_hmatrix_ranks")
+        return r
+
+    def device_bytes(self):
+        nb = C.c_int64()
+        _check(_lib().h2_hmatrix_ranks(self._h, None, None, None, C.byref(nb)), "h2_hmatrix_ranks")
+        return nb.value
+
+    def to_dense(self):
+        out = np.empty(self.shape, dtype=np.float64, order="F")
+        _check(_lib().h2_hmatrix_to_dense(self._h, out.ctypes.data_as(C.c_void_p), 0), "h2_hmatrix_to_dense")
+        return np.ascontiguousarray(out)
+
+    def free(self):
+        if self._h:
+            _lib().h2_hmatrix_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mul_h(A: H2Matrix, B: H2Matrix, eps: float, max_rank: int = 0, sync: bool = True, stream=None) -> HMatrix:
+    """C ~ A*B as an H-matrix (accumulation and agglomeration, no nested-basis recompression)."""
+    o = MulOpts()
+    o.theta, o.max_rank, o.precision, o.sync = 0.0, int(max_rank), 0, 1 if sync else 0
+    o.stream = stream
+    h = C.c_void_p()
+    _check(_lib().h2_mul_h(A.handle, B.handle, float(eps), C.byref(o), C.byref(h)), "h2_mul_h")
+    return HMatrix(h.value, A.info().n, B.info().n)
 
 
 def mul_profile(A: H2Matrix, B: H2Matrix, eps: float, prof, max_rank: int = 0, stream=None,
