@@ -188,6 +188,31 @@ int h2_hmatrix_ranks(const h2_hmatrix* C, int* ranks, int* nadm, int* rank_max, 
 
 void h2_hmatrix_free(h2_hmatrix* C);
 
+/* ---- Serving: continuous batching of products ---------------------------
+ * A server runs products C = A*B (h2_mul semantics) over operands the caller
+ * keeps resident.  Requests queue in arrival order; a dispatcher thread admits
+ * the oldest as soon as one of `slots` streams is free and the device memory
+ * the request needs fits `mem_budget`: a further instance of its plan
+ * (workspace, control block, graph) when all instances are busy, plus the
+ * output.  Admitted products run concurrently, so requests that arrive while
+ * others are on the GPU overlap with them.  Results are bitwise the same as
+ * the same products run alone (same plan, same kernels).
+ *   h2_server_create  slots 1..64; mem_budget in bytes (0: 90% of the free
+ *                     device memory at creation)
+ *   h2_server_submit  enqueues; opts->stream and opts->sync are ignored; A and
+ *                     B must stay alive until the request is collected
+ *   h2_server_wait    blocks until the request is done; returns C (free with
+ *                     h2_free) and optionally the milliseconds from submit to
+ *                     start and from submit to completion
+ *   h2_server_destroy drops requests not yet started, waits for running ones,
+ *                     frees uncollected results */
+typedef struct h2_server h2_server;
+int h2_server_create(int slots, int64_t mem_budget, h2_server** out);
+int h2_server_submit(h2_server* s, const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts,
+                     int64_t* ticket);
+int h2_server_wait(h2_server* s, int64_t ticket, h2_matrix** C, double* queued_ms, double* total_ms);
+void h2_server_destroy(h2_server* s);
+
 /* Dense n x n column-major expansion (caller ordering) into `out` (host or device). */
 int h2_to_dense(const h2_matrix* A, double* out, int on_device);
 

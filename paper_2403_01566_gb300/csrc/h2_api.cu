@@ -12,9 +12,13 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <list>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/h2.h"
@@ -68,7 +72,8 @@ static int lib_init() {
 // --------------------------------------------------- plan device state ----
 struct PlanRT {
   std::shared_ptr<Plan> plan;
-  void* d_blob = nullptr;      // job arrays + slot init + idx + konst + rank_src
+  std::shared_ptr<PlanRT> blob_owner;  // clones: the instance whose job arrays they use
+  void* d_blob = nullptr;      // job arrays + slot init + idx + konst + rank_src (owner only)
   DeviceJobs dj;
   int* d_slot_init = nullptr;
   int* d_idx = nullptr;
@@ -427,18 +432,27 @@ static uint64_t matrix_sig(const h2_matrix* M) {
   return h;
 }
 
-// Product plans (with their device job arrays, workspace and graph), shared
-// by every operand pair of the same structure; least recently used first out.
+// Product plans, shared by every operand pair of the same structure; least
+// recently used first out.  An entry holds the host plan and one or more
+// device instances: instance 0 owns the job arrays, further instances (for
+// products of the same structure running at once, see h2_server) share them
+// and have their own workspace, control block, graph and completion event.
 struct PlanKey {
   uint64_t a, b;
   int opt;
   bool operator==(const PlanKey& o) const { return a == o.a && b == o.b && opt == o.opt; }
 };
+struct PlanEntry {
+  std::shared_ptr<Plan> plan;
+  std::mutex mu;  // guards inst
+  std::vector<std::shared_ptr<PlanRT>> inst;
+  std::vector<int> rank_src;
+};
 constexpr size_t PLAN_CACHE_MAX = 4;
 std::mutex g_plans_mu;
-std::list<std::pair<PlanKey, std::shared_ptr<PlanRT>>> g_plans;  // most recent first
+std::list<std::pair<PlanKey, std::shared_ptr<PlanEntry>>> g_plans;  // most recent first
 
-static std::shared_ptr<PlanRT> plan_lookup(const PlanKey& k) {
+static std::shared_ptr<PlanEntry> plan_lookup(const PlanKey& k) {
   std::lock_guard<std::mutex> lk(g_plans_mu);
   for (auto it = g_plans.begin(); it != g_plans.end(); ++it)
     if (it->first == k) {
@@ -448,11 +462,11 @@ static std::shared_ptr<PlanRT> plan_lookup(const PlanKey& k) {
   return nullptr;
 }
 
-static void plan_insert(const PlanKey& k, std::shared_ptr<PlanRT> rt) {
-  std::shared_ptr<PlanRT> evicted;
+static void plan_insert(const PlanKey& k, std::shared_ptr<PlanEntry> e) {
+  std::shared_ptr<PlanEntry> evicted;
   {
     std::lock_guard<std::mutex> lk(g_plans_mu);
-    g_plans.emplace_front(k, std::move(rt));
+    g_plans.emplace_front(k, std::move(e));
     if (g_plans.size() > PLAN_CACHE_MAX) {
       evicted = std::move(g_plans.back().second);  // released outside the lock
       g_plans.pop_back();
@@ -461,11 +475,43 @@ static void plan_insert(const PlanKey& k, std::shared_ptr<PlanRT> rt) {
 }
 
 static void plan_cache_clear() {
-  std::list<std::pair<PlanKey, std::shared_ptr<PlanRT>>> old;
+  std::list<std::pair<PlanKey, std::shared_ptr<PlanEntry>>> old;
   {
     std::lock_guard<std::mutex> lk(g_plans_mu);
     old.swap(g_plans);
   }
+}
+
+// Device bytes of one instance of a plan beyond the shared job arrays.
+static int64_t instance_bytes(const Plan& P) {
+  return (P.ws_len + P.fac_len) * 8 + 512 + 16 * (int64_t)P.nscal + 4 * (int64_t)P.slot_init.size() + 64;
+}
+
+// A further instance sharing the job arrays of `base`.
+static int clone_instance(const std::shared_ptr<PlanRT>& base, std::shared_ptr<PlanRT>& out) {
+  auto rt = std::make_shared<PlanRT>();
+  rt->plan = base->plan;
+  rt->blob_owner = base;
+  rt->dj = base->dj;
+  rt->d_slot_init = base->d_slot_init;
+  rt->d_idx = base->d_idx;
+  rt->d_konst = base->d_konst;
+  rt->d_rank_src = base->d_rank_src;
+  rt->nrank = base->nrank;
+  rt->svd_smem = base->svd_smem;
+  const Plan& P = *rt->plan;
+  const size_t nslot = std::max<size_t>(P.slot_init.size(), 1);
+  const size_t sz = 512 + 16 * (size_t)P.nscal + 4 * nslot + 64;
+  CK(cudaMalloc(&rt->d_ctrl, sz));
+  rt->d_ctx = (ExecCtx*)rt->d_ctrl;
+  rt->d_scal = (double*)(rt->d_ctrl + 512);
+  rt->d_nrm = rt->d_scal + P.nscal;
+  rt->d_slot = (int*)(rt->d_nrm + P.nscal);
+  rt->d_err = rt->d_slot + nslot;
+  CK(cudaMalloc(&rt->d_ws, std::max<int64_t>(P.ws_len + P.fac_len, 1) * sizeof(double)));
+  CK(cudaEventCreateWithFlags(&rt->last, cudaEventDisableTiming));
+  out = rt;
+  return H2_OK;
 }
 
 // Batched matrix-vector products: plans per (matrix structure, nrhs), and the
@@ -669,60 +715,80 @@ void h2_free(h2_matrix* A) {
 static int hmul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts,
                      h2_hmatrix** Cout);
 
-static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts, h2_kernel_prof* prof,
-                    h2_matrix** Cout) {
-  if (!Cout) return H2_EINVAL;
-  *Cout = nullptr;
+// Validated arguments of a product.
+struct MulArgs {
+  h2_matrix* A = nullptr;
+  h2_matrix* B = nullptr;
+  double eps = 0, theta = 0.25;
+  int max_rank = 0, precision = 0;
+  bool sync = true;
+  cudaStream_t stream = nullptr;
+  PlanKey key{};
+};
+
+static int mul_args(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts, MulArgs& m) {
   if (!Ac || !Bc || !(eps >= 0.0) || !std::isfinite(eps)) return H2_EINVAL;
-  h2_matrix* A = const_cast<h2_matrix*>(Ac);
-  h2_matrix* B = const_cast<h2_matrix*>(Bc);
-  if (A->cols->hash != B->rows->hash || A->cols->n != B->rows->n) return H2_ETREE;
-  if (A->kpad != B->kpad) return H2_EINVAL;
-  double theta = (opts && opts->theta > 0.0) ? opts->theta : 0.25;
-  if (!(theta < 0.5)) return H2_EINVAL;
-  const int max_rank = opts ? opts->max_rank : 0;
-  const int precision = opts ? opts->precision : 0;
-  if (precision != 0 && precision != 1) return H2_EINVAL;
-  if (max_rank < 0 || max_rank > GEMM_MAXTILE) return H2_EINVAL;
-  const bool sync = opts ? opts->sync != 0 : true;
-  cudaStream_t s = (opts && opts->stream) ? (cudaStream_t)opts->stream : g_stream;
-  int rc = lib_init();
-  if (rc) return rc;
-  if ((rc = ensure_level_bases(A, s)) || (rc = ensure_level_bases(B, s))) return rc;
-  // plan: shared by all operand pairs of the same structure
-  const PlanKey key{matrix_sig(A), matrix_sig(B),
-                    (precision * 100 + max_rank) * 1000 + (int)std::lround(theta * 997.0)};
-  std::shared_ptr<PlanRT> rt = plan_lookup(key);
-  if (!rt) {
-    MulOptions mo;
-    mo.eta = A->eta;
-    mo.theta = theta;
-    mo.max_rank = max_rank;
-    mo.precision = precision;
-    std::shared_ptr<Plan> plan;
-    try {
-      plan = make_product_plan(desc_of(A), desc_of(B), mo);
-    } catch (const std::exception& ex) {
-      g_last_cuda = ex.what();
-      return H2_EINVAL;
-    }
-    std::vector<int> rank_src;
-    rank_src.insert(rank_src.end(), plan->rank_row_slot.begin(), plan->rank_row_slot.end());
-    rank_src.insert(rank_src.end(), plan->rank_col_slot.begin(), plan->rank_col_slot.end());
-    rt = std::make_shared<PlanRT>();
-    rt->plan = plan;
-    rc = upload_plan(*rt, rank_src);
-    if (rc == H2_ENOMEM) {
-      // the cached plans hold device memory: release them and retry once
-      plan_cache_clear();
-      rt = std::make_shared<PlanRT>();
-      rt->plan = plan;
-      rc = upload_plan(*rt, rank_src);
-    }
-    if (rc) return rc;
-    plan_insert(key, rt);
+  m.A = const_cast<h2_matrix*>(Ac);
+  m.B = const_cast<h2_matrix*>(Bc);
+  if (m.A->cols->hash != m.B->rows->hash || m.A->cols->n != m.B->rows->n) return H2_ETREE;
+  if (m.A->kpad != m.B->kpad) return H2_EINVAL;
+  m.eps = eps;
+  m.theta = (opts && opts->theta > 0.0) ? opts->theta : 0.25;
+  if (!(m.theta < 0.5)) return H2_EINVAL;
+  m.max_rank = opts ? opts->max_rank : 0;
+  m.precision = opts ? opts->precision : 0;
+  if (m.precision != 0 && m.precision != 1) return H2_EINVAL;
+  if (m.max_rank < 0 || m.max_rank > GEMM_MAXTILE) return H2_EINVAL;
+  m.sync = opts ? opts->sync != 0 : true;
+  m.stream = (opts && opts->stream) ? (cudaStream_t)opts->stream : g_stream;
+  m.key = PlanKey{matrix_sig(m.A), matrix_sig(m.B),
+                  (m.precision * 100 + m.max_rank) * 1000 + (int)std::lround(m.theta * 997.0)};
+  return H2_OK;
+}
+
+// The cached plan entry of a product (planned and uploaded on a miss).
+static int mul_entry(const MulArgs& m, std::shared_ptr<PlanEntry>& e) {
+  e = plan_lookup(m.key);
+  if (e) return H2_OK;
+  MulOptions mo;
+  mo.eta = m.A->eta;
+  mo.theta = m.theta;
+  mo.max_rank = m.max_rank;
+  mo.precision = m.precision;
+  auto ne = std::make_shared<PlanEntry>();
+  try {
+    ne->plan = make_product_plan(desc_of(m.A), desc_of(m.B), mo);
+  } catch (const std::exception& ex) {
+    g_last_cuda = ex.what();
+    return H2_EINVAL;
   }
-  Plan& P = *rt->plan;
+  ne->rank_src = ne->plan->rank_row_slot;
+  ne->rank_src.insert(ne->rank_src.end(), ne->plan->rank_col_slot.begin(), ne->plan->rank_col_slot.end());
+  auto rt = std::make_shared<PlanRT>();
+  rt->plan = ne->plan;
+  int rc = upload_plan(*rt, ne->rank_src);
+  if (rc == H2_ENOMEM) {
+    // the cached plans hold device memory: release them and retry once
+    plan_cache_clear();
+    rt = std::make_shared<PlanRT>();
+    rt->plan = ne->plan;
+    rc = upload_plan(*rt, ne->rank_src);
+  }
+  if (rc) return rc;
+  ne->inst.push_back(rt);
+  plan_insert(m.key, ne);
+  e = ne;
+  return H2_OK;
+}
+
+// Enqueues the product on stream s with plan instance rt; *Cout holds C,
+// whose `done` event marks its completion.
+static int enqueue_product(const MulArgs& m, PlanRT& rt, cudaStream_t s, h2_kernel_prof* prof, h2_matrix** Cout) {
+  h2_matrix* A = m.A;
+  h2_matrix* B = m.B;
+  int rc;
+  if ((rc = ensure_level_bases(A, s)) || (rc = ensure_level_bases(B, s))) return rc;
+  Plan& P = *rt.plan;
   auto C = new h2_matrix();
   C->dim = A->dim;
   C->eta = A->eta;
@@ -747,13 +813,14 @@ static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   C->stream = s;
   if (cudaMallocAsync(&C->d_arena, C->arena_len * sizeof(double), s) != cudaSuccess ||
       cudaMallocAsync(&C->d_int, (2 * C->rows->ncl + 1) * sizeof(int), s) != cudaSuccess) {
-    delete C;
+    cudaGetLastError();
+    h2_free(C);
     return H2_ENOMEM;
   }
   cudaMemsetAsync(C->d_arena, 0, P.c_len * sizeof(double), s);
-  const double params[PARAM_COUNT] = {eps / 4.0 * std::sqrt(1.0 - 2.0 * theta), eps / 3.0};
-  rc = prof ? run_plan_profiled(*rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, prof)
-            : run_plan(*rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, true);
+  const double params[PARAM_COUNT] = {m.eps / 4.0 * std::sqrt(1.0 - 2.0 * m.theta), m.eps / 3.0};
+  rc = prof ? run_plan_profiled(rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, prof)
+            : run_plan(rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, true);
   if (rc) {
     h2_free(C);
     return rc;
@@ -761,10 +828,29 @@ static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   cudaEventCreateWithFlags(&C->done, cudaEventDisableTiming);
   cudaEventRecord(C->done, s);
   *Cout = C;
-  if (sync) {
-    rc = h2_check(C);
+  return H2_OK;
+}
+
+static int mul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts, h2_kernel_prof* prof,
+                    h2_matrix** Cout) {
+  if (!Cout) return H2_EINVAL;
+  *Cout = nullptr;
+  MulArgs m;
+  int rc = mul_args(Ac, Bc, eps, opts, m);
+  if (rc) return rc;
+  if ((rc = lib_init())) return rc;
+  std::shared_ptr<PlanEntry> e;
+  if ((rc = mul_entry(m, e))) return rc;
+  std::shared_ptr<PlanRT> rt;
+  {
+    std::lock_guard<std::mutex> lk(e->mu);
+    rt = e->inst[0];  // replays of one instance are ordered by its event
+  }
+  if ((rc = enqueue_product(m, *rt, m.stream, prof, Cout))) return rc;
+  if (m.sync) {
+    rc = h2_check(*Cout);
     if (rc) {
-      h2_free(C);
+      h2_free(*Cout);
       *Cout = nullptr;
       return rc;
     }
@@ -790,30 +876,37 @@ static int hmul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const
   if (rc) return rc;
   if ((rc = ensure_level_bases(A, s)) || (rc = ensure_level_bases(B, s))) return rc;
   const PlanKey key{matrix_sig(A), matrix_sig(B), -1 - max_rank};  // H-matrix plans: negative option codes
-  std::shared_ptr<PlanRT> rt = plan_lookup(key);
-  if (!rt) {
+  std::shared_ptr<PlanEntry> ent = plan_lookup(key);
+  if (!ent) {
     MulOptions mo;
     mo.eta = A->eta;
     mo.max_rank = max_rank;
     mo.hmatrix = true;
-    std::shared_ptr<Plan> plan;
+    ent = std::make_shared<PlanEntry>();
     try {
-      plan = make_product_plan(desc_of(A), desc_of(B), mo);
+      ent->plan = make_product_plan(desc_of(A), desc_of(B), mo);
     } catch (const std::exception& ex) {
       g_last_cuda = ex.what();
       return H2_EINVAL;
     }
-    rt = std::make_shared<PlanRT>();
-    rt->plan = plan;
-    rc = upload_plan(*rt, plan->rank_row_slot);
+    ent->rank_src = ent->plan->rank_row_slot;
+    auto rt0 = std::make_shared<PlanRT>();
+    rt0->plan = ent->plan;
+    rc = upload_plan(*rt0, ent->rank_src);
     if (rc == H2_ENOMEM) {
       plan_cache_clear();
-      rt = std::make_shared<PlanRT>();
-      rt->plan = plan;
-      rc = upload_plan(*rt, plan->rank_row_slot);
+      rt0 = std::make_shared<PlanRT>();
+      rt0->plan = ent->plan;
+      rc = upload_plan(*rt0, ent->rank_src);
     }
     if (rc) return rc;
-    plan_insert(key, rt);
+    ent->inst.push_back(rt0);
+    plan_insert(key, ent);
+  }
+  std::shared_ptr<PlanRT> rt;
+  {
+    std::lock_guard<std::mutex> elk(ent->mu);
+    rt = ent->inst[0];
   }
   const Plan& P = *rt->plan;
   auto C = new h2_hmatrix();
@@ -1057,6 +1150,302 @@ int h2_to_dense(const h2_matrix* Ac, double* out, int on_device) {
   if (on_device) CK(cudaMemcpy(out, o.data(), o.size() * 8, cudaMemcpyHostToDevice));
   else std::memcpy(out, o.data(), o.size() * 8);
   return H2_OK;
+}
+
+}  // extern "C"
+
+// ================================================================= server ====
+// Continuous batching of products over resident operands.  Requests queue in
+// arrival order; a dispatcher thread admits the oldest ones as soon as a
+// stream slot is free and the device memory they need (a further instance of
+// their plan when all of its instances are busy, plus the output) fits the
+// budget.  Admitted products run concurrently on their own streams, so the
+// small stages and tails of one overlap the work of the others.  A host
+// callback on each stream marks completion and wakes the dispatcher.
+namespace h2 {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct SrvReq {
+  int64_t ticket = 0;
+  MulArgs m;
+  Clock::time_point t_submit, t_start, t_done;
+  h2_matrix* C = nullptr;
+  int rc = H2_OK;
+  int slot = -1;
+  std::shared_ptr<PlanRT> inst;
+  int64_t out_bytes = 0;
+  bool finished = false;   // device work done (callback) or failed at launch
+};
+
+}  // namespace
+}  // namespace h2
+
+struct h2_server {
+  int nslots = 0;
+  int64_t budget = 0, used = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<bool> slot_busy;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::shared_ptr<h2::SrvReq>> pending;
+  std::map<int64_t, std::shared_ptr<h2::SrvReq>> live;  // submitted and not yet collected
+  std::map<h2::PlanRT*, bool> inst_busy;                // instances in use by this server
+  std::vector<std::shared_ptr<h2::PlanEntry>> entries;  // entries this server holds instances of
+  int64_t next_ticket = 1;
+  bool stop = false;
+  std::thread dispatcher;
+};
+
+namespace h2 {
+namespace {
+
+struct DoneArg {
+  h2_server* srv;
+  std::shared_ptr<SrvReq> req;
+};
+
+// Marks a request done and frees its stream slot and plan instance (the
+// work before it on the stream has completed).  Bookkeeping only: no CUDA
+// calls, as it runs as a stream host function.  Caller holds srv->mu.
+void release_locked(h2_server* S, SrvReq& r) {
+  r.t_done = Clock::now();
+  r.finished = true;
+  if (r.slot >= 0) S->slot_busy[r.slot] = false;
+  if (r.inst) S->inst_busy[r.inst.get()] = false;
+  r.slot = -1;
+  r.inst.reset();
+}
+
+void CUDART_CB on_done(void* p) {
+  auto* d = static_cast<DoneArg*>(p);
+  {
+    std::lock_guard<std::mutex> lk(d->srv->mu);
+    release_locked(d->srv, *d->req);
+  }
+  d->srv->cv.notify_all();
+  delete d;
+}
+
+// Output bytes of a product (its arena and integer array).
+int64_t output_bytes(const Plan& P, const h2_matrix* A, const h2_matrix* B) {
+  return 8 * (P.c_len + (int64_t)(A->rows->depth + 1) * A->rows->n * P.kpad +
+              (int64_t)(B->cols->depth + 1) * B->cols->n * P.kpad) +
+         4 * (2 * (int64_t)A->rows->ncl + 1);
+}
+
+// Tries to start the oldest pending request; false when it has to wait.
+bool try_admit(h2_server* S, std::unique_lock<std::mutex>& lk) {
+  if (S->pending.empty()) return false;
+  int slot = -1;
+  for (int i = 0; i < S->nslots; ++i)
+    if (!S->slot_busy[i]) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return false;
+  auto req = S->pending.front();
+  // plan entry (planning runs without the lock)
+  lk.unlock();
+  std::shared_ptr<PlanEntry> e;
+  int rc = mul_entry(req->m, e);
+  lk.lock();
+  if (S->pending.empty() || S->pending.front() != req) return true;  // dropped meanwhile: look again
+  if (rc) {
+    S->pending.pop_front();
+    req->rc = rc;
+    req->finished = true;
+    return true;
+  }
+  std::vector<std::shared_ptr<PlanRT>> insts;
+  {
+    std::lock_guard<std::mutex> elk(e->mu);
+    insts = e->inst;
+  }
+  if (std::find(S->entries.begin(), S->entries.end(), e) == S->entries.end()) {
+    S->entries.push_back(e);
+    S->used += instance_bytes(*e->plan) * (int64_t)insts.size();
+  }
+  const int64_t out_b = output_bytes(*e->plan, req->m.A, req->m.B);
+  std::shared_ptr<PlanRT> inst;
+  for (auto& i : insts)
+    if (!S->inst_busy[i.get()]) {
+      inst = i;
+      break;
+    }
+  bool any_running = false;
+  for (bool b : S->slot_busy) any_running |= b;
+  if (!inst) {
+    const int64_t need = instance_bytes(*e->plan);
+    if (S->used + need + out_b > S->budget && any_running) return false;  // wait for memory
+    lk.unlock();
+    rc = clone_instance(insts[0], inst);
+    lk.lock();
+    if (rc == H2_OK) {
+      std::lock_guard<std::mutex> elk(e->mu);
+      e->inst.push_back(inst);
+      S->used += need;
+    }
+    if (S->pending.empty() || S->pending.front() != req) return true;  // dropped meanwhile: look again
+    if (rc) {
+      if (!any_running) {  // nothing in flight to wait for: fail the request
+        S->pending.pop_front();
+        req->rc = rc;
+        req->finished = true;
+        return true;
+      }
+      return false;
+    }
+  } else if (S->used + out_b > S->budget && any_running) {
+    return false;  // wait for memory; alone it runs regardless
+  }
+  S->pending.pop_front();
+  S->slot_busy[slot] = true;
+  S->inst_busy[inst.get()] = true;
+  req->slot = slot;
+  req->inst = inst;
+  req->out_bytes = out_b;
+  S->used += out_b;
+  req->t_start = Clock::now();
+  lk.unlock();
+  cudaStream_t st = S->streams[slot];
+  rc = enqueue_product(req->m, *inst, st, nullptr, &req->C);
+  if (rc == H2_OK) {
+    auto* d = new DoneArg{S, req};
+    if (cudaLaunchHostFunc(st, on_done, d) != cudaSuccess) {
+      delete d;
+      cudaStreamSynchronize(st);
+      lk.lock();
+      release_locked(S, *req);
+      return true;
+    }
+    lk.lock();
+  } else {
+    lk.lock();
+    req->rc = rc;
+    release_locked(S, *req);
+  }
+  return true;
+}
+
+void dispatch_loop(h2_server* S) {
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    if (S->stop && S->pending.empty()) break;
+    bool progressed = false;
+    while (try_admit(S, lk)) progressed = true;
+    if (progressed) {
+      S->cv.notify_all();
+      continue;
+    }
+    S->cv.wait(lk);
+  }
+}
+
+}  // namespace
+}  // namespace h2
+
+extern "C" {
+
+int h2_server_create(int slots, int64_t mem_budget, h2_server** out) {
+  if (!out || slots < 1 || slots > 64 || mem_budget < 0) return H2_EINVAL;
+  *out = nullptr;
+  int rc = lib_init();
+  if (rc) return rc;
+  auto S = new h2_server();
+  S->nslots = slots;
+  if (mem_budget == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      delete S;
+      return H2_ECUDA;
+    }
+    mem_budget = (int64_t)(0.9 * (double)fr);
+  }
+  S->budget = mem_budget;
+  S->slot_busy.assign(slots, false);
+  for (int i = 0; i < slots; ++i) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto x : S->streams) cudaStreamDestroy(x);
+      delete S;
+      return H2_ECUDA;
+    }
+    S->streams.push_back(st);
+  }
+  S->dispatcher = std::thread(dispatch_loop, S);
+  *out = S;
+  return H2_OK;
+}
+
+int h2_server_submit(h2_server* S, const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts* opts,
+                     int64_t* ticket) {
+  if (!S || !ticket) return H2_EINVAL;
+  auto req = std::make_shared<SrvReq>();
+  int rc = mul_args(A, B, eps, opts, req->m);
+  if (rc) return rc;
+  req->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return H2_EINVAL;
+    req->ticket = S->next_ticket++;
+    S->pending.push_back(req);
+    S->live[req->ticket] = req;
+    *ticket = req->ticket;
+  }
+  S->cv.notify_all();
+  return H2_OK;
+}
+
+int h2_server_wait(h2_server* S, int64_t ticket, h2_matrix** C, double* queued_ms, double* total_ms) {
+  if (!S || !C) return H2_EINVAL;
+  *C = nullptr;
+  std::shared_ptr<SrvReq> req;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->live.find(ticket);
+    if (it == S->live.end()) return H2_EINVAL;
+    req = it->second;
+    S->cv.wait(lk, [&] { return req->finished; });
+    S->live.erase(it);
+    S->used -= req->out_bytes;
+  }
+  S->cv.notify_all();
+  auto ms = [](Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
+  if (queued_ms) *queued_ms = req->rc == H2_OK ? ms(req->t_submit, req->t_start) : 0.0;
+  if (total_ms) *total_ms = req->rc == H2_OK ? ms(req->t_submit, req->t_done) : 0.0;
+  if (req->rc != H2_OK) return req->rc;
+  const int rc = h2_check(req->C);
+  if (rc) {
+    h2_free(req->C);
+    return rc;
+  }
+  *C = req->C;
+  return H2_OK;
+}
+
+void h2_server_destroy(h2_server* S) {
+  if (!S) return;
+  {
+    // requests not yet admitted are dropped; running ones finish
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    for (auto& r : S->pending) {
+      r->rc = H2_EINVAL;
+      r->finished = true;
+    }
+    S->pending.clear();
+  }
+  S->cv.notify_all();
+  if (S->dispatcher.joinable()) S->dispatcher.join();
+  for (auto st : S->streams) cudaStreamSynchronize(st);
+  for (auto& kv : S->live)
+    if (kv.second->C) h2_free(kv.second->C);
+  for (auto st : S->streams) cudaStreamDestroy(st);
+  delete S;
 }
 
 }  // extern "C"

@@ -72,6 +72,11 @@ def _lib():
                                          C.POINTER(C.c_int64)]
         lib.h2_hmatrix_free.argtypes = [vp]
         lib.h2_hmatrix_free.restype = None
+        lib.h2_server_create.argtypes = [C.c_int, i64, C.POINTER(vp)]
+        lib.h2_server_submit.argtypes = [vp, vp, vp, C.c_double, C.POINTER(MulOpts), C.POINTER(i64)]
+        lib.h2_server_wait.argtypes = [vp, i64, C.POINTER(vp), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.h2_server_destroy.argtypes = [vp]
+        lib.h2_server_destroy.restype = None
         lib.h2_to_dense.argtypes = [vp, vp, C.c_int]
         lib.h2_info.argtypes = [vp, C.POINTER(Stats)]
         lib.h2_ranks.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -247,6 +252,47 @@ def mul_h(A: H2Matrix, B: H2Matrix, eps: float, max_rank: int = 0, sync: bool = 
     h = C.c_void_p()
     _check(_lib().h2_mul_h(A.handle, B.handle, float(eps), C.byref(o), C.byref(h)), "h2_mul_h")
     return HMatrix(h.value, A.info().n, B.info().n)
+
+
+class Server:
+    """Continuous batching of products (h2_server_*): submit() returns a ticket
+    at once, wait(ticket) returns (C, queued_ms, total_ms)."""
+
+    def __init__(self, slots: int = 4, mem_budget: int = 0):
+        h = C.c_void_p()
+        _check(_lib().h2_server_create(int(slots), int(mem_budget), C.byref(h)), "h2_server_create")
+        self._h = h.value
+        self._keep = {}  # operands of requests not yet collected
+
+    def submit(self, A: H2Matrix, B: H2Matrix, eps: float, max_rank: int = 0, precision: int = 0) -> int:
+        o = MulOpts()
+        o.theta, o.max_rank, o.precision, o.sync = 0.0, int(max_rank), int(precision), 1
+        t = C.c_int64()
+        _check(_lib().h2_server_submit(self._h, A.handle, B.handle, float(eps), C.byref(o), C.byref(t)),
+               "h2_server_submit")
+        self._keep[t.value] = (A, B)
+        return t.value
+
+    def wait(self, ticket: int):
+        h = C.c_void_p()
+        q, tot = C.c_double(), C.c_double()
+        try:
+            _check(_lib().h2_server_wait(self._h, int(ticket), C.byref(h), C.byref(q), C.byref(tot)), "h2_server_wait")
+        finally:
+            self._keep.pop(ticket, None)
+        return H2Matrix(h.value), q.value, tot.value
+
+    def close(self):
+        if self._h:
+            _lib().h2_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mul_profile(A: H2Matrix, B: H2Matrix, eps: float, prof, max_rank: int = 0, stream=None,
