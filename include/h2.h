@@ -79,7 +79,12 @@ typedef struct {
  *                  products with FP32 sums from the FP64 data; agglomeration,
  *                  condensation, QR, SVD, rank decisions and norms stay FP64.
  *                  Adds about 1e-7 relative rounding to each block; the bound
- *                  eps still holds for eps >= 1e-6.  Other values: H2_EINVAL.
+ *                  eps still holds for eps >= 1e-6, but the rounding sits above
+ *                  the agglomeration tolerance and raises ranks.
+ *              2 = compensated FP32 contractions in every GEMM stage: operands
+ *                  split into FP32 hi + lo parts, error-free products and
+ *                  compensated sums (about 1e-13 relative); QR, SVD, rank
+ *                  decisions and norms stay FP64.  Other values: H2_EINVAL.
  *   sync       1 = return after the product is complete and report device errors;
  *              0 = return after enqueueing (errors are reported by h2_check)
  *   stream     cudaStream_t to run on, or NULL for the library stream */

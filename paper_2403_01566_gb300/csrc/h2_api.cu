@@ -715,6 +715,22 @@ void h2_free(h2_matrix* A) {
 static int hmul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const h2_mul_opts* opts,
                      h2_hmatrix** Cout);
 
+// Squared relative noise floor of the Jacobi SVDs of a product (PARAM_SVD_FLOOR).
+// Columns below floor * ||M||_F are rounding noise of the contractions that
+// formed M; resolving them to relative precision costs sweeps and changes no
+// kept singular value.  FP64: eps * 2^-20 clamped to [2^-50, 2^-40], i.e. at
+// least 2^20 below the tightest relative truncation tolerance of the product
+// (eps/3/(2n^2) with n <= 8 in the agglomeration, and the basis tolerances);
+// eps = 0 keeps every direction above 2^-50.  Compensated contractions
+// (~1e-13 rounding): 2^-40.
+static double svd_noise_floor(double eps, int precision) {
+  double f;
+  if (precision == 2) f = 9.094947017729282e-13;  // 2^-40
+  else if (eps > 0.0) f = std::min(9.094947017729282e-13, std::max(8.881784197001252e-16, eps * 9.5367431640625e-07));
+  else f = 8.881784197001252e-16;  // 2^-50
+  return f * f;
+}
+
 // Validated arguments of a product.
 struct MulArgs {
   h2_matrix* A = nullptr;
@@ -737,7 +753,7 @@ static int mul_args(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   if (!(m.theta < 0.5)) return H2_EINVAL;
   m.max_rank = opts ? opts->max_rank : 0;
   m.precision = opts ? opts->precision : 0;
-  if (m.precision != 0 && m.precision != 1) return H2_EINVAL;
+  if (m.precision < 0 || m.precision > 2) return H2_EINVAL;
   if (m.max_rank < 0 || m.max_rank > GEMM_MAXTILE) return H2_EINVAL;
   m.sync = opts ? opts->sync != 0 : true;
   m.stream = (opts && opts->stream) ? (cudaStream_t)opts->stream : g_stream;
@@ -818,7 +834,8 @@ static int enqueue_product(const MulArgs& m, PlanRT& rt, cudaStream_t s, h2_kern
     return H2_ENOMEM;
   }
   cudaMemsetAsync(C->d_arena, 0, P.c_len * sizeof(double), s);
-  const double params[PARAM_COUNT] = {m.eps / 4.0 * std::sqrt(1.0 - 2.0 * m.theta), m.eps / 3.0};
+  const double params[PARAM_COUNT] = {m.eps / 4.0 * std::sqrt(1.0 - 2.0 * m.theta), m.eps / 3.0,
+                                       svd_noise_floor(m.eps, m.precision)};
   rc = prof ? run_plan_profiled(rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, prof)
             : run_plan(rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, true);
   if (rc) {
@@ -927,7 +944,7 @@ static int hmul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const
   }
   cudaMemsetAsync(C->d_arena, 0, C->arena_len * sizeof(double), s);
   cudaMemsetAsync(C->d_int, 0, nint * sizeof(int), s);
-  const double params[PARAM_COUNT] = {0.0, eps / 3.0};
+  const double params[PARAM_COUNT] = {0.0, eps / 3.0, svd_noise_floor(eps, 0)};
   rc = run_plan(*rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, true);
   if (rc) {
     h2_hmatrix_free(C);

@@ -49,22 +49,88 @@ __device__ __forceinline__ double ld_op(const double* p, int ld, int t, int i, i
   return t ? p[(int64_t)j * ld + i] : p[(int64_t)i * ld + j];
 }
 
-// acc[q] += op(A)(m x k) op(B)(k x n) for the outputs of this thread, in the
-// compute type T (double, or float for the FP32 contractions: operands are
-// rounded to FP32 when staged, products and sums are FP32)
-template <int Q, typename T>
-__device__ __forceinline__ void gemm_accumulate(T (&acc)[Q], int nq, int m, int n, int k, const double* A,
-                                                int lda, int ta, const double* B, int ldb, int tb, T* As,
-                                                T* Bs, int ldbs) {
+// Compute modes of the grouped GEMM.  Operands are FP64 arrays; each inner
+// product over k runs in the mode's arithmetic, its result is combined in
+// FP64 (alpha, further terms, beta).
+//   GM_F64  FP64 products and sums
+//   GM_F32  operands rounded to FP32, FP32 products and sums (~1e-7)
+//   GM_DF   compensated: operands split into FP32 hi + lo parts (a = hi + lo
+//           to ~2^-48), the hi*hi product error-free via FMA, sums by TwoSum
+//           (Knuth), the hi*lo and lo*hi cross terms and all error terms in a
+//           second FP32 word (Ogita, Rump and Oishi, "Accurate sum and dot
+//           product", SIAM J. Sci. Comput. 26, 2005); ~1e-13 relative at FP32
+//           issue rates.  The error-free steps use the non-contracting
+//           __fmul_rn / __fadd_rn / __fsub_rn intrinsics.
+enum GemmMode : int { GM_F64 = 0, GM_F32 = 1, GM_DF = 2 };
+
+struct DF {
+  float s, c;
+};
+
+template <int MODE>
+struct GemmPol;
+
+template <>
+struct GemmPol<GM_F64> {
+  using S = double;  // staged operand
+  using A = double;  // inner accumulator
+  __device__ static S stage(double v) { return v; }
+  __device__ static A zero() { return 0.0; }
+  __device__ static void fma_acc(A& a, S x, S y) { a = fma(x, y, a); }
+  __device__ static double value(const A& a) { return a; }
+};
+
+template <>
+struct GemmPol<GM_F32> {
+  using S = float;
+  using A = float;
+  __device__ static S stage(double v) { return (float)v; }
+  __device__ static A zero() { return 0.0f; }
+  __device__ static void fma_acc(A& a, S x, S y) { a = fmaf(x, y, a); }
+  __device__ static double value(const A& a) { return (double)a; }
+};
+
+template <>
+struct GemmPol<GM_DF> {
+  using S = float2;  // (hi, lo)
+  using A = DF;
+  __device__ static S stage(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  }
+  __device__ static A zero() { return DF{0.0f, 0.0f}; }
+  __device__ static void fma_acc(A& a, S x, S y) {
+    const float p = __fmul_rn(x.x, y.x);
+    const float e = fmaf(x.x, y.x, -p);  // x.hi * y.hi = p + e exactly
+    const float t = __fadd_rn(a.s, p);   // TwoSum(a.s, p) = t + err exactly
+    const float z = __fsub_rn(t, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    a.s = t;
+    float c = __fadd_rn(a.c, err);
+    c = __fadd_rn(c, e);
+    c = fmaf(x.x, y.y, c);
+    c = fmaf(x.y, y.x, c);
+    a.c = c;
+  }
+  __device__ static double value(const A& a) { return (double)a.s + (double)a.c; }
+};
+
+// acc[q] += op(A)(m x k) op(B)(k x n) for the outputs of this thread
+template <int Q, int MODE>
+__device__ __forceinline__ void gemm_accumulate(typename GemmPol<MODE>::A (&acc)[Q], int nq, int m, int n, int k,
+                                                const double* A, int lda, int ta, const double* B, int ldb, int tb,
+                                                typename GemmPol<MODE>::S* As, typename GemmPol<MODE>::S* Bs,
+                                                int ldbs) {
+  using P = GemmPol<MODE>;
   for (int kk = 0; kk < k; kk += GK) {
     const int kc = min(GK, k - kk);
     for (int e = threadIdx.x; e < m * kc; e += 256) {
       const int r = e / kc, l = e % kc;
-      As[r * (GK + 1) + l] = (T)ld_op(A, lda, ta, r, kk + l);
+      As[r * (GK + 1) + l] = P::stage(ld_op(A, lda, ta, r, kk + l));
     }
     for (int e = threadIdx.x; e < kc * n; e += 256) {
       const int l = e / n, c = e % n;
-      Bs[l * ldbs + c] = (T)ld_op(B, ldb, tb, kk + l, c);
+      Bs[l * ldbs + c] = P::stage(ld_op(B, ldb, tb, kk + l, c));
     }
     __syncthreads();
 #pragma unroll
@@ -73,8 +139,8 @@ __device__ __forceinline__ void gemm_accumulate(T (&acc)[Q], int nq, int m, int 
         const int e = threadIdx.x + 256 * q;
         if (e < m * n) {
           const int r = e / n, c = e % n;
-          T a = acc[q];
-          for (int l = 0; l < kc; ++l) a = fma(As[r * (GK + 1) + l], Bs[l * ldbs + c], a);
+          typename P::A a = acc[q];
+          for (int l = 0; l < kc; ++l) P::fma_acc(a, As[r * (GK + 1) + l], Bs[l * ldbs + c]);
           acc[q] = a;
         }
       }
@@ -85,25 +151,27 @@ __device__ __forceinline__ void gemm_accumulate(T (&acc)[Q], int nq, int m, int 
 
 // Shared memory of a stage whose outputs are at most mmax rows and whose
 // right factors (and inner widths of three-factor terms) at most nb columns:
-// As mmax x (GK+1), Bs GK x (nb+1), Ts mmax x (nb+1).  Stages of small
-// static shapes thus keep many CTAs resident per SM.
+// As mmax x (GK+1), Bs GK x (nb+1), Ts mmax x (nb+1) staged operands (8 bytes
+// each in the FP64 and compensated modes, 4 in the FP32 mode).  Stages of
+// small static shapes thus keep many CTAs resident per SM.
 __host__ __device__ constexpr int gemm_smem_doubles(int mmax, int nb) {
   return mmax * (GK + 1) + (GK + mmax) * (nb + 1);
 }
 
 // Q = outputs per thread (m * n <= 256 Q): small stages take a small Q, so
-// fewer registers and more resident CTAs per SM.  T = compute type (double;
-// float for the FP32-contraction form).  Inputs and outputs are FP64 arrays.
-template <int Q, typename T>
+// fewer registers and more resident CTAs per SM.  MODE = compute mode (above).
+template <int Q, int MODE>
 __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs,
                                               const GemmTerm* __restrict__ terms, int mmax, int nb) {
+  using P = GemmPol<MODE>;
+  using S = typename P::S;
   const ExecCtx& x = *px;
   extern __shared__ double sm_raw[];
-  T* sm = reinterpret_cast<T*>(sm_raw);
+  S* sm = reinterpret_cast<S*>(sm_raw);
   const int ldbs = nb + 1;
-  T* As = sm;                      // mmax x (GK+1)
-  T* Bs = As + mmax * (GK + 1);    // GK x (nb+1)
-  T* Ts = Bs + GK * ldbs;          // mmax x (nb+1)
+  S* As = sm;                      // mmax x (GK+1)
+  S* Bs = As + mmax * (GK + 1);    // GK x (nb+1)
+  S* Ts = Bs + GK * ldbs;          // mmax x (nb+1)
   const GemmOut& O = outs[blockIdx.x];
   const int m = dimv(O.m, x.slot);
   const int n = O.clampn ? min(dimv(O.n, x.slot), GT) : dimv(O.n, x.slot);
@@ -113,15 +181,14 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     return;
   }
   const int nq = (m * n + 255) / 256;
-  T acc[Q];
+  double acc[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) acc[q] = 0.0;
 
   for (int ti = O.t0; ti < O.t1; ++ti) {
     const GemmTerm& Tm = terms[ti];
-    double alpha_d = Tm.alpha;
-    if (Tm.scale_idx >= 0) alpha_d *= x.scal[Tm.scale_idx];
-    const T alpha = (T)alpha_d;
+    double alpha = Tm.alpha;
+    if (Tm.scale_idx >= 0) alpha *= x.scal[Tm.scale_idx];
     const double* A = ptrv(Tm.a, x);
     const double* B = ptrv(Tm.b, x);
     const double* C = ptrv(Tm.c, x);
@@ -129,18 +196,18 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const int e = threadIdx.x + 256 * q;
-        if (q < nq && e < m * n) acc[q] += alpha * (T)ld_op(A, Tm.lda, Tm.ta, e / n, e % n);
+        if (q < nq && e < m * n) acc[q] = fma(alpha, ld_op(A, Tm.lda, Tm.ta, e / n, e % n), acc[q]);
       }
       continue;
     }
     const int k1 = dimv(Tm.k1, x.slot);
+    typename P::A tacc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) tacc[q] = P::zero();
     if (C == nullptr) {
-      T tacc[Q];
+      gemm_accumulate<Q, MODE>(tacc, nq, m, n, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) tacc[q] = 0.0;
-      gemm_accumulate(tacc, nq, m, n, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
-#pragma unroll
-      for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
+      for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, P::value(tacc[q]), acc[q]);
       continue;
     }
     // three-factor term: Ts = op(A)op(B) (m x nn), then acc += alpha * Ts op(C)
@@ -150,24 +217,21 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
       return;
     }
     const int nq2 = (m * nn + 255) / 256;
-    T tacc[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) tacc[q] = 0.0;
-    gemm_accumulate(tacc, nq2, m, nn, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
+    gemm_accumulate<Q, MODE>(tacc, nq2, m, nn, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int e = threadIdx.x + 256 * q;
-      if (q < nq2 && e < m * nn) Ts[(e / nn) * ldbs + e % nn] = tacc[q];
+      if (q < nq2 && e < m * nn) Ts[(e / nn) * ldbs + e % nn] = P::stage(P::value(tacc[q]));
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < Q; ++q) tacc[q] = 0.0;
+    for (int q = 0; q < Q; ++q) tacc[q] = P::zero();
     // Ts (m x nn) times op(C) (nn x n); Ts plays the role of A (already in smem)
     for (int kk = 0; kk < nn; kk += GK) {
       const int kc = min(GK, nn - kk);
       for (int e = threadIdx.x; e < kc * n; e += 256) {
         const int l = e / n, c = e % n;
-        Bs[l * ldbs + c] = (T)ld_op(C, Tm.ldc, Tm.tc, kk + l, c);
+        Bs[l * ldbs + c] = P::stage(ld_op(C, Tm.ldc, Tm.tc, kk + l, c));
       }
       __syncthreads();
 #pragma unroll
@@ -176,8 +240,8 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
           const int e = threadIdx.x + 256 * q;
           if (e < m * n) {
             const int r = e / n, c = e % n;
-            T a = tacc[q];
-            for (int l = 0; l < kc; ++l) a = fma(Ts[r * ldbs + kk + l], Bs[l * ldbs + c], a);
+            typename P::A a = tacc[q];
+            for (int l = 0; l < kc; ++l) P::fma_acc(a, Ts[r * ldbs + kk + l], Bs[l * ldbs + c]);
             tacc[q] = a;
           }
         }
@@ -185,7 +249,7 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, tacc[q], acc[q]);
+    for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, P::value(tacc[q]), acc[q]);
   }
   double* out = ptrv(O.o, x);
 #pragma unroll
@@ -193,7 +257,7 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     const int e = threadIdx.x + 256 * q;
     if (q < nq && e < m * n) {
       double* p = out + (int64_t)(e / n) * O.ldo + e % n;
-      *p = O.beta ? (*p + (double)acc[q]) : (double)acc[q];
+      *p = O.beta ? (*p + acc[q]) : acc[q];
     }
   }
 }
@@ -696,8 +760,9 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
     s_fro = f;
   }
   __syncthreads();
-  // columns below 2^-50 ||M||_F are rounding noise: never rotated, sigma = 0
-  const double tiny2 = s_fro * 7.888609052210118e-31;
+  // columns below the noise floor (2^-50 ||M||_F for FP64 inputs) are
+  // rounding noise: never rotated, sigma = 0
+  const double tiny2 = s_fro * x.scal[PARAM_SVD_FLOOR];
   const int ce = cols + (cols & 1);
   const int npairs = ce / 2;
   const double tol = 2.5e-15;
@@ -1006,12 +1071,12 @@ cudaError_t kernels_init() {
   if (g_attr_done) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   const int gsm = (int)gemm_smem_bytes();
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<4, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<GQ, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<4, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<GQ, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+#define H2_GEMM_ATTR(Q, M) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<Q, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+  H2_GEMM_ATTR(1, GM_F64) H2_GEMM_ATTR(4, GM_F64) H2_GEMM_ATTR(GQ, GM_F64)
+  H2_GEMM_ATTR(1, GM_F32) H2_GEMM_ATTR(4, GM_F32) H2_GEMM_ATTR(GQ, GM_F32)
+  H2_GEMM_ATTR(1, GM_DF) H2_GEMM_ATTR(4, GM_DF) H2_GEMM_ATTR(GQ, GM_DF)
+#undef H2_GEMM_ATTR
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes(NORM_MAXN));
   if (e != cudaSuccess) return e;
@@ -1028,32 +1093,39 @@ void launch_finalize(const ExecCtx* x, int nrank, cudaStream_t s) {
   k_finalize<<<(nrank + 255) / 256 + 1, 256, 0, s>>>(x);
 }
 
+template <int MODE>
+static void launch_gemm_mode(int cells, int count, size_t sm, cudaStream_t s, const ExecCtx* x, const GemmOut* go,
+                             const GemmTerm* gt, int mmax, int nb) {
+  if (cells <= 256)
+    k_gemm<1, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+  else if (cells <= 1024)
+    k_gemm<4, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+  else
+    k_gemm<GQ, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+}
+
+static void launch_gemm(int mode, int cells, int count, size_t sm, cudaStream_t s, const ExecCtx* x,
+                        const GemmOut* go, const GemmTerm* gt, int mmax, int nb) {
+  if (mode == GM_DF)
+    launch_gemm_mode<GM_DF>(cells, count, sm, s, x, go, gt, mmax, nb);
+  else if (mode == GM_F32)
+    launch_gemm_mode<GM_F32>(cells, count, sm, s, x, go, gt, mmax, nb);
+  else
+    launch_gemm_mode<GM_F64>(cells, count, sm, s, x, go, gt, mmax, nb);
+}
+
 void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t svd_smem, cudaStream_t s) {
   if (st.count <= 0) return;
   switch (st.kind) {
     case ST_GEMM:
     {
-      const int shape = st.aux & ~GEMM_AUX_FP32;
+      const int shape = st.aux & ~(GEMM_AUX_FP32 | GEMM_AUX_DF);
       const int mmax = shape ? ((shape >> 16) & 0xff) : GT, nb = shape ? (shape & 0xffff) : GT;
-      const bool f32 = (st.aux & GEMM_AUX_FP32) != 0;
-      const size_t sm = (f32 ? sizeof(float) : sizeof(double)) * gemm_smem_doubles(mmax, nb);
+      const int mode = (st.aux & GEMM_AUX_DF) ? GM_DF : (st.aux & GEMM_AUX_FP32) ? GM_F32 : GM_F64;
+      const size_t sm = (mode == GM_F32 ? sizeof(float) : sizeof(double)) * gemm_smem_doubles(mmax, nb);
       const int cells = mmax * nb;
       const GemmOut* go = j.gemm_out + st.first;
-      if (f32) {
-        if (cells <= 256)
-          k_gemm<1, float><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
-        else if (cells <= 1024)
-          k_gemm<4, float><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
-        else
-          k_gemm<GQ, float><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
-      } else {
-        if (cells <= 256)
-          k_gemm<1, double><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
-        else if (cells <= 1024)
-          k_gemm<4, double><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
-        else
-          k_gemm<GQ, double><<<st.count, 256, sm, s>>>(x, go, j.gemm_term, mmax, nb);
-      }
+      launch_gemm(mode, cells, st.count, sm, s, x, go, j.gemm_term, mmax, nb);
     }
       break;
     case ST_COPY:

@@ -9,6 +9,7 @@ namespace h2 {
 constexpr int SVD_MAXDIM = 256;  // largest Jacobi SVD (rows and columns)
 constexpr int NORM_MAXN = 128;   // largest matrix of a spectral-norm job
 constexpr int GEMM_AUX_FP32 = 1 << 24;  // Stage::aux flag of a GEMM stage: FP32 products and sums
+constexpr int GEMM_AUX_DF = 1 << 25;    // Stage::aux flag of a GEMM stage: compensated FP32 (double-float)
 constexpr int SVD_SMEM_MATRIX_DOUBLES = 129 * 64;  // SVD matrices up to this size sit in shared memory (66 KB)
 
 #ifdef __CUDACC__

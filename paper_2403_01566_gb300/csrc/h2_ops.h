@@ -157,6 +157,12 @@ struct Stage {
   int aux;        // GEMM stages: (largest m << 16) | largest n or inner width (0: 64, 64)
 };
 
+// Indices into the per-product parameter block (ExecCtx::scal[0..]).
+// PARAM_SVD_FLOOR: squared relative noise floor of the Jacobi SVD (columns
+// with ||m||^2 below it times ||M||_F^2 count as rounding noise: sigma = 0,
+// never rotated); set per product from eps and the contraction precision.
+enum ParamIdx : int { PARAM_TOL_BASIS = 0, PARAM_TOL_AGG = 1, PARAM_SVD_FLOOR = 2, PARAM_COUNT = 3 };
+
 // Kernel parameters common to all stages.
 // It lives in device memory (one control block per plan) so that a captured
 // CUDA graph of the stage list can be replayed with new operand pointers.

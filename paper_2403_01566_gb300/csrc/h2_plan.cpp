@@ -114,6 +114,7 @@ struct Builder {
 
   explicit Builder(Plan& p) : P(p) {}
   bool fp32_contractions = false;  // precision form 1
+  bool df_contractions = false;    // precision form 2
   int64_t alloc(int64_t n) {
     const int64_t o = ws;
     ws += (std::max<int64_t>(n, 1) + 31) & ~int64_t(31);
@@ -171,7 +172,9 @@ struct Builder {
     // pushes, dense leaf products) and the coupling projection; agglomeration,
     // condensation and the bases stay FP64
     const bool f32 = fp32_contractions && (tag <= 9 || tag == 14);  // TAG_P .. TAG_DENSE, TAG_COUPLE
-    P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag, 0, (g_mmax << 16) | g_nb | (f32 ? GEMM_AUX_FP32 : 0)});
+    // compensated contractions (~1e-13): every GEMM stage
+    const int mode_flag = df_contractions ? GEMM_AUX_DF : f32 ? GEMM_AUX_FP32 : 0;
+    P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag, 0, (g_mmax << 16) | g_nb | mode_flag});
     go.clear();
     gt.clear();
     g_mmax = g_nb = 1;
@@ -335,6 +338,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   Plan& P = *plan;
   Builder B(P);
   B.fp32_contractions = opt.precision == 1;
+  B.df_contractions = opt.precision == 2;
   const Tree& TI = *X.rows;
   const Tree& TJ = *X.cols;
   const Tree& TK = *Y.cols;

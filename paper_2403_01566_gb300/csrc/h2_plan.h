@@ -29,12 +29,13 @@ struct MulOptions {
   double eta = 2.0;      // admissibility of the target block tree
   double theta = 0.25;   // weight factor (Section 5.3)
   int max_rank = 0;      // cap of the adaptive ranks (storage padding of C)
-  int precision = 0;     // 0 FP64 throughout; 1 FP32 contractions (accumulation and couplings)
+  int precision = 0;     // 0 FP64 throughout; 1 FP32 contractions (accumulation and couplings);
+                         // 2 compensated FP32 contractions (all GEMM stages)
   bool hmatrix = false;  // H-matrix output: stop after agglomeration (no nested-basis recompression)
 };
 
 // Indices into the per-product parameter block (ExecCtx::scal[0..]).
-enum ParamIdx : int { PARAM_TOL_BASIS = 0, PARAM_TOL_AGG = 1, PARAM_COUNT = 2 };
+// Indices of the per-product parameters: see ParamIdx in h2_ops.h.
 
 struct Plan {
   std::vector<Stage> stages;

@@ -188,3 +188,20 @@ def test_plan_shared_by_operands_of_the_same_structure():
     res1 = O.multiply(X1, Y1, 1e-6)
     d1, _ = blockrel(C1.to_dense(), res1.C.dense(), X1.dense() @ Y1.dense(), res1.C.blocks)
     assert d1 <= 1e-10, d1
+
+
+@pytest.mark.parametrize("m", [32, 64])
+def test_grid_eps_1e8_with_rank_cap_64(m):
+    """eps = 1e-8 (the tightest tolerance of the 2D grid workload) with
+    max_rank = 64: same result and ranks as the oracle."""
+    w = I.grid_2d(m)
+    A, B = gpu_pair(w)
+    C = h2.mul(A, B, 1e-8, max_rank=64)
+    X, Y = build_pair(w)
+    res = O.multiply(X, Y, 1e-8)
+    Z = X.dense() @ Y.dense()
+    d_oracle, d_exact = blockrel(C.to_dense(), res.C.dense(), Z, res.C.blocks)
+    assert d_oracle <= 1e-10, d_oracle
+    assert d_exact <= 1e-8, d_exact
+    rr, rc = C.ranks()
+    assert list(rr) == [res.ranks_row[c.id] for c in O.all_clusters(X.rows)]

@@ -71,11 +71,39 @@ def test_fp32_contractions_within_eps(w, eps):
     assert np.all(np.abs(np.asarray(rc) - co) <= np.maximum(2, 0.25 * co))
 
 
+CASES_DF = [
+    (I.plain_1d(1024), 1e-6),
+    (I.grid_2d(64), 1e-6),
+    (I.grid_2d(32), 1e-4),
+    (I.sphere_3d(2048), 1e-6),
+    (I.cube_3d(2048, seed=13, leaf=64, order=4), 1e-6),
+]
+
+
+@pytest.mark.parametrize("w,eps", CASES_DF, ids=[f"{w.name}-{e:g}" for w, e in CASES_DF])
+def test_compensated_contractions_match_oracle(w, eps):
+    """precision 2: compensated FP32 contractions (~1e-13) keep the FP64
+    result: within 1e-10 of the oracle and identical ranks."""
+    A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
+    B = h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order)
+    Cdf = h2.mul(A, B, eps, precision=2)
+    X, Y = build_pair(w)
+    res = O.multiply(X, Y, eps)
+    Z = X.dense() @ Y.dense()
+    d_oracle, d_exact = _blockrel(Cdf.to_dense(), res.C.dense(), Z, res.C.blocks)
+    print(f"\n{w.name} eps={eps:g}: compensated form vs oracle {d_oracle:.3e}, vs exact {d_exact:.3e}")
+    assert d_oracle <= 1e-10, d_oracle
+    assert d_exact <= eps, d_exact
+    rr, rc = Cdf.ranks()
+    assert list(rr) == [res.ranks_row[c.id] for c in O.all_clusters(X.rows)]
+    assert list(rc) == [res.ranks_col[c.id] for c in O.all_clusters(Y.cols)]
+
+
 def test_precision_values():
     w = I.plain_1d(256)
     A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
     with pytest.raises(h2.H2Error):
-        h2.mul(A, A, 1e-6, precision=2)
+        h2.mul(A, A, 1e-6, precision=3)
     # the FP64 and FP32 forms have separate cached plans
     C1 = h2.mul(A, A, 1e-6, precision=1)
     C0 = h2.mul(A, A, 1e-6, precision=0)
