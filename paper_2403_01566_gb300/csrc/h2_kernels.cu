@@ -305,6 +305,21 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Householder reflector of x = [alpha; x2] with s2 = ||x2||^2 > 0:
+// beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta = 1 + |alpha| / ||x||,
+// v = [1; x2 / (alpha - beta)].  Written with one reciprocal square root and
+// one reciprocal instead of a square root and two divisions: every FP64
+// instruction costs a full warp issue on this GPU, and this runs once per
+// column on the critical path.
+__device__ __forceinline__ void householder_scalars(double alpha, double s2, double& beta, double& tau, double& sc) {
+  const double n2 = fma(alpha, alpha, s2);
+  const double r = rsqrt(n2);
+  const double nrm = n2 * r;
+  beta = -copysign(nrm, alpha);
+  tau = fma(fabs(alpha), r, 1.0);
+  sc = copysign(__drcp_rn(fabs(alpha) + nrm), alpha);
+}
+
 constexpr int QR_MAXPIV = 256;  // largest column count of a pivoted QR
 
 // Householder QR on a column-major matrix a (rows x cols, leading dimension
@@ -379,9 +394,8 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
       const double alpha = col[j];
       double t = 0.0, sc = 0.0;
       if (s2 > 0.0) {
-        const double beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-        t = (beta - alpha) / beta;
-        sc = 1.0 / (alpha - beta);
+        double beta;
+        householder_scalars(alpha, s2, beta, t, sc);
         for (int i = j + 1 + lane; i < rows; i += 32) col[i] *= sc;
         __syncwarp();
         if (lane == 0) col[j] = beta;
@@ -478,9 +492,8 @@ __device__ void tsqr_r(const double* __restrict__ a, int lda, int rows, int cols
         const double alpha = W[j * ld + j];
         double t = 0.0;
         if (s2 > 0.0) {
-          const double beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-          t = (beta - alpha) / beta;
-          const double sc = 1.0 / (alpha - beta);
+          double beta, sc;
+          householder_scalars(alpha, s2, beta, t, sc);
           for (int i = lane; i < ch; i += 32) cj[i] *= sc;
           __syncwarp();
           if (lane == 0) W[j * ld + j] = beta;
@@ -942,11 +955,7 @@ __global__ void __launch_bounds__(256) k_norm(const ExecCtx* __restrict__ px, co
     if (threadIdx.x == 0) {
       const double alpha = G[(k + 1) * ld + k];
       double tau = 0.0, sc = 0.0, beta = alpha;
-      if (s2 > 0.0) {
-        beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-        tau = (beta - alpha) / beta;
-        sc = 1.0 / (alpha - beta);
-      }
+      if (s2 > 0.0) householder_scalars(alpha, s2, beta, tau, sc);
       sh[0] = tau;
       sh[1] = sc;
       e[k] = beta;
