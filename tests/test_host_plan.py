@@ -1,0 +1,98 @@
+"""CPU test of the planner (host logic): the stage lists that the CUDA
+kernels execute, run by a plain CPU interpreter of the stage semantics
+(tests/host/stage_interpreter.cpp), must reproduce the oracle's product:
+within 1e-10 block-relative (the FP64 tolerance) with identical adaptive
+ranks, on 1D, 2D, 3D and ragged cases, and for the H-matrix output variant
+against the oracle's pre-recompression factors.  No GPU is involved; the
+interpreter links only the planner and the host tree / Chebyshev code."""
+import os
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import h2oracle as O
+from paper_2403_01566_gb300 import inputs as I
+from tests.oracle_cases import build_pair
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2403_01566_gb300", "csrc")
+
+
+@pytest.fixture(scope="session")
+def interpreter(tmp_path_factory):
+    gxx = shutil.which("g++")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    if not gxx or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path_factory.mktemp("interp") / "stage_interpreter")
+    cmd = [gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-o", exe,
+           os.path.join(ROOT, "tests", "host", "stage_interpreter.cpp"),
+           os.path.join(CSRC, "h2_plan.cpp"), os.path.join(CSRC, "h2_build.cpp"),
+           "-I", os.path.join(ROOT, "include"), "-I", cuda_inc]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return exe
+
+
+def run_interpreter(exe, w, eps, tmp_path, hmatrix=False, max_rank=0):
+    pts = tmp_path / "pts.bin"
+    out = tmp_path / "out.bin"
+    np.ascontiguousarray(w.points, dtype=np.float64).tofile(pts)
+    ka, kb = w.kernel_a, w.kernel_b
+    args = [exe, str(pts), str(w.n), str(w.dim), str(w.leaf_size), str(w.order), repr(w.eta), repr(eps),
+            str(ka.kind), repr(ka.scale), repr(ka.diag), repr(ka.width),
+            str(kb.kind), repr(kb.scale), repr(kb.diag), repr(kb.width), str(max_rank), "1" if hmatrix else "0",
+            str(out)]
+    r = subprocess.run(args, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    raw = np.fromfile(out, dtype=np.uint8)
+    n = w.n
+    D = np.frombuffer(raw[:8 * n * n].tobytes(), dtype=np.float64).reshape(n, n)
+    ranks = np.frombuffer(raw[8 * n * n:].tobytes(), dtype=np.int32)
+    return D, ranks
+
+
+def worst_blockrel(D, Dref, Z, blocks):
+    worst = 0.0
+    for b in O.block_leaves(blocks):
+        ix = np.ix_(b.t.idx, b.s.idx)
+        nz = np.linalg.norm(Z[ix], 2) or 1.0
+        worst = max(worst, np.linalg.norm(D[ix] - Dref[ix], 2) / nz)
+    return worst
+
+
+CASES = [
+    (I.grid_2d(32), 1e-6),
+    (I.plain_1d(1000), 1e-4),                     # ragged leaves
+    (I.square_2d(1500, seed=7, leaf=32, order=3), 1e-6),
+    (I.cube_3d(1200, seed=11, leaf=40, order=2), 1e-4),
+]
+
+
+@pytest.mark.parametrize("w,eps", CASES, ids=[f"{w.name}-{e:g}" for w, e in CASES])
+def test_planned_stages_reproduce_the_oracle(interpreter, tmp_path, w, eps):
+    D, ranks = run_interpreter(interpreter, w, eps, tmp_path)
+    X, Y = build_pair(w)
+    res = O.multiply(X, Y, eps)
+    Z = X.dense() @ Y.dense()
+    assert worst_blockrel(D, res.C.dense(), Z, res.C.blocks) <= 1e-10
+    ncl = len(ranks) // 2
+    assert list(ranks[:ncl]) == [res.ranks_row[c.id] for c in O.all_clusters(X.rows)]
+    assert list(ranks[ncl:]) == [res.ranks_col[c.id] for c in O.all_clusters(Y.cols)]
+
+
+def test_planned_hmatrix_variant_reproduces_the_oracle_factors(interpreter, tmp_path):
+    w = I.grid_2d(32)
+    D, _ = run_interpreter(interpreter, w, 1e-6, tmp_path, hmatrix=True)
+    X, Y = build_pair(w)
+    res = O.multiply(X, Y, 1e-6)
+    Do = res.C.dense()
+    for b in O.block_leaves(res.C.blocks):
+        if b.adm:
+            L, R = res.factors[id(b)]
+            Do[np.ix_(b.t.idx, b.s.idx)] = L @ R.T
+    Z = X.dense() @ Y.dense()
+    assert worst_blockrel(D, Do, Z, res.C.blocks) <= 1e-10
