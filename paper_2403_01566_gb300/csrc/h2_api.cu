@@ -86,7 +86,6 @@ struct PlanRT {
   int* d_slot = nullptr;
   int* d_err = nullptr;
   double* d_ws = nullptr;
-  size_t svd_smem = 0;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t last = nullptr;  // completion of the last replay (workspace reuse)
   int nrank = 0;
@@ -149,7 +148,6 @@ static int upload_plan(PlanRT& rt, const std::vector<int>& rank_src) {
   rt.d_slot = (int*)(rt.d_nrm + P.nscal);
   rt.d_err = rt.d_slot + nslot;
   CK(cudaMalloc(&rt.d_ws, std::max<int64_t>(P.ws_len + P.fac_len, 1) * sizeof(double)));
-  rt.svd_smem = svd_smem_bytes(P.svd_maxrows, P.svd_maxcols);
   CK(cudaEventCreateWithFlags(&rt.last, cudaEventDisableTiming));
   return H2_OK;
 }
@@ -205,7 +203,7 @@ static int run_plan(PlanRT& rt, double* bx, double* by, double* bc, int* out_int
     if (!P.slot_init.empty())
       cudaMemcpyAsync(rt.d_slot, rt.d_slot_init, sizeof(int) * P.slot_init.size(), cudaMemcpyDeviceToDevice, cs);
     cudaMemsetAsync(rt.d_err, 0, sizeof(int), cs);
-    for (const Stage& st : P.stages) launch_stage(st, rt.d_ctx, rt.dj, rt.svd_smem, cs);
+    for (const Stage& st : P.stages) launch_stage(st, rt.d_ctx, rt.dj, cs);
     launch_finalize(rt.d_ctx, rt.nrank, cs);
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
@@ -220,7 +218,7 @@ static int run_plan(PlanRT& rt, double* bx, double* by, double* bc, int* out_int
     if (!P.slot_init.empty())
       CK(cudaMemcpyAsync(rt.d_slot, rt.d_slot_init, sizeof(int) * P.slot_init.size(), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(rt.d_err, 0, sizeof(int), s));
-    for (const Stage& st : P.stages) launch_stage(st, rt.d_ctx, rt.dj, rt.svd_smem, s);
+    for (const Stage& st : P.stages) launch_stage(st, rt.d_ctx, rt.dj, s);
     launch_finalize(rt.d_ctx, rt.nrank, s);
   }
   CK(cudaGetLastError());
@@ -264,7 +262,7 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
   for (auto& e : ev) CK(cudaEventCreate(&e));
   for (size_t i = 0; i < ns; ++i) {
     CK(cudaEventRecord(ev[2 * i], s));
-    launch_stage(P.stages[i], rt.d_ctx, rt.dj, rt.svd_smem, s);
+    launch_stage(P.stages[i], rt.d_ctx, rt.dj, s);
     CK(cudaEventRecord(ev[2 * i + 1], s));
   }
   CK(cudaEventRecord(ev[2 * ns], s));
@@ -298,7 +296,8 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
     const Stage& st = P.stages[i];
     pr.jobs += st.count;
     double st_fl = 0.0;
-    double sw_sum = 0.0, sw_max = 0.0, rows_sum = 0.0, cols_sum = 0.0;
+    double sw_sum = 0.0, sw_max = 0.0, rows_sum = 0.0, cols_sum = 0.0, rows_max = 0.0, cols_max = 0.0;
+    double glob_jobs = 0.0, glob_fl = 0.0;  // SVD jobs whose matrix stays in global memory
     for (int j = 0; j < st.count; ++j) {
       double fl = 0, by = 0;
       const int64_t J = st.first + j;
@@ -363,6 +362,12 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
           sw_max = std::max(sw_max, (double)sweeps[2 * J]);
           rows_sum += r;
           cols_sum += c;
+          rows_max = std::max(rows_max, r);
+          cols_max = std::max(cols_max, c);
+          if (svd_colarr_doubles((int)c) + (r + 1) * c > st.smem / 8) {
+            glob_jobs += 1;
+            glob_fl += fl;
+          }
           break;
         }
         default:
@@ -376,8 +381,9 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
       std::fprintf(stderr, "stage %4zu kind %d tag %2d jobs %7d smem %6d ms %9.4f gflop %9.4f tflops %6.3f", i,
                    st.kind, st.tag, st.count, st.smem, ms, st_fl / 1e9, ms > 0 ? st_fl / ms / 1e9 : 0.0);
       if (st.kind == ST_SVD && st.count > 0)
-        std::fprintf(stderr, " rows %.1f cols %.1f sweeps %.2f max %.0f", rows_sum / st.count, cols_sum / st.count,
-                     sw_sum / st.count, sw_max);
+        std::fprintf(stderr, " rows %.1f cols %.1f sweeps %.2f max %.0f | max rows %.0f cols %.0f | in global %.0f jobs %.3f gflop",
+                     rows_sum / st.count, cols_sum / st.count, sw_sum / st.count, sw_max, rows_max, cols_max, glob_jobs,
+                     glob_fl / 1e9);
       std::fprintf(stderr, "\n");
     }
   }
@@ -498,7 +504,6 @@ static int clone_instance(const std::shared_ptr<PlanRT>& base, std::shared_ptr<P
   rt->d_konst = base->d_konst;
   rt->d_rank_src = base->d_rank_src;
   rt->nrank = base->nrank;
-  rt->svd_smem = base->svd_smem;
   const Plan& P = *rt->plan;
   const size_t nslot = std::max<size_t>(P.slot_init.size(), 1);
   const size_t sz = 512 + 16 * (size_t)P.nscal + 4 * nslot + 64;

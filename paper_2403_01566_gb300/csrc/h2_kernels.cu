@@ -527,6 +527,21 @@ __device__ void tsqr_r(const double* __restrict__ a, int lda, int rows, int cols
 constexpr int QR_TSQR_MAXC = 64;       // widest R-only factorisation that streams row chunks
 constexpr int QR_MAX_SMEM_BYTES = 8 * (QR_TSQR_MAXC + 64) * QR_TSQR_MAXC;  // 64 KB
 
+// R output of a QR job (see QrJob::rmode): R(i, c) = src[c * lds + i] above
+// the diagonal for i < q, zero elsewhere.  Call after a block barrier (the
+// pivot order and src are complete).
+__device__ void write_r(const QrJob& J, double* r, const double* src, int64_t lds, int cols, int q, const int* piv) {
+  const bool unpiv = (J.rmode & 1) && piv;
+  const bool trans = (J.rmode & 2) != 0;
+  for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
+    // consecutive threads write consecutive addresses of r
+    const int i = trans ? e % cols : e / cols, c = trans ? e / cols : e % cols;
+    const double v = (src && c >= i && i < q) ? src[(int64_t)c * lds + i] : 0.0;
+    const int dc = unpiv ? piv[c] : c;
+    r[trans ? (int64_t)dc * J.ldr + i : (int64_t)i * J.ldr + dc] = v;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, const QrJob* __restrict__ jobs,
                                             int smem_doubles) {
   const ExecCtx& x = *px;
@@ -547,8 +562,7 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
   const int lda = J.lda;
   const int q = min(rows, cols);
   if (rows <= 0 || cols <= 0) {
-    if (r)
-      for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) r[(int64_t)(e / cols) * J.ldr + e % cols] = 0.0;
+    if (r) write_r(J, r, nullptr, 0, cols, 0, nullptr);
     if (piv)
       for (int c = threadIdx.x; c < cols; c += blockDim.x) piv[c] = c;
     return;
@@ -566,11 +580,7 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
         const int c = (int)(e / rows), i = (int)(e % rows);
         a[(int64_t)c * lda + i] = sm[e];
       }
-    if (r)
-      for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
-        const int i = e / cols, c = e % cols;
-        r[(int64_t)i * J.ldr + c] = (c >= i && i < q) ? sm[(int64_t)c * rows + i] : 0.0;
-      }
+    if (r) write_r(J, r, sm, rows, cols, q, piv);
     return;
   }
   if (!J.keep && cols <= QR_TSQR_MAXC && smem_doubles / cols - cols >= 16) {
@@ -582,20 +592,12 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
     if (piv) householder_cols(sm, ld, cols, cols, nullptr, sh, piv, cn, cn0);
     if (tau)
       for (int c = threadIdx.x; c < q; c += blockDim.x) tau[c] = 0.0;
-    if (r)
-      for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
-        const int i = e / cols, c = e % cols;
-        r[(int64_t)i * J.ldr + c] = (c >= i && i < q) ? sm[(int64_t)c * ld + i] : 0.0;
-      }
+    if (r) write_r(J, r, sm, ld, cols, q, piv);
     return;
   }
   // general case: in place in global memory
   householder_cols(a, lda, rows, cols, tau, sh, piv, cn, cn0);
-  if (r)
-    for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) {
-      const int i = e / cols, c = e % cols;
-      r[(int64_t)i * J.ldr + c] = (c >= i && i < q) ? a[(int64_t)c * lda + i] : 0.0;
-    }
+  if (r) write_r(J, r, a, lda, cols, q, piv);
 }
 
 // out = H_0 ... H_{q-1} [Y; 0].  Threads: column c = tid % nc of out, row
@@ -685,7 +687,7 @@ __device__ __forceinline__ int svd_pair_j(int rnd, int p, int ce) {
   return max(svd_pair_a(rnd, p, ce), svd_pair_b(rnd, p, ce));
 }
 
-__global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, const SvdJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, const SvdJob* __restrict__ jobs,
                                              int64_t first, int smem_doubles, int cmax) {
   const ExecCtx& x = *px;
   extern __shared__ double sdyn[];
@@ -694,17 +696,19 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
   __shared__ int nround;
   __shared__ double part[256];  // partial dot products (blockDim <= 256)
   __shared__ double s_fro;
-  double* nrm2 = sdyn;                 // squared column norms
-  double* dsc = nrm2 + cmax;           // column scales d of M = Mt diag(d)
-  double* dinv = dsc + cmax;           // 1/d
-  double* snorm = dinv + cmax;         // singular values
-  double* rfa = snorm + cmax;          // rotation factors of the round's rotating pairs
-  double* rfb = rfa + (cmax / 2 + 1);
-  int* spos = reinterpret_cast<int*>(rfb + (cmax / 2 + 1));  // sorted position of each column
-  int* rlist = spos + cmax;            // rotating pairs of the round: (i << 16) | j
-  double* sm = sdyn + svd_colarr_doubles(cmax);
   const SvdJob& J = jobs[blockIdx.x];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
+  // per-column arrays sized for this job's columns, the matrix behind them
+  const int ca = svd_colarr_doubles(cols);
+  double* nrm2 = sdyn;                 // squared column norms
+  double* dsc = nrm2 + cols;           // column scales d of M = Mt diag(d)
+  double* dinv = dsc + cols;           // 1/d
+  double* snorm = dinv + cols;         // singular values
+  double* rfa = snorm + cols;          // rotation factors of the round's rotating pairs
+  double* rfb = rfa + (cols / 2 + 1);
+  int* spos = reinterpret_cast<int*>(rfb + (cols / 2 + 1));  // sorted position of each column
+  int* rlist = spos + cols;            // rotating pairs of the round: (i << 16) | j
+  double* sm = sdyn + ca;
   int* rank_out = (J.rank_slot >= 0) ? x.slot + J.rank_slot : nullptr;
   if (rows <= 0 || cols <= 0) {
     if (threadIdx.x == 0) {
@@ -716,7 +720,8 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
     }
     return;
   }
-  if (rows > SVD_MAXDIM || cols > cmax || ((int64_t)(rows + 1) * cols > smem_doubles && !J.trans)) {
+  const bool fits = ca + (int64_t)(rows + 1) * cols <= smem_doubles;
+  if (rows > SVD_MAXDIM || cols > cmax || ca > smem_doubles || (!fits && !J.trans)) {
     if (threadIdx.x == 0) {
       set_err(x, -9);
       if (rank_out) *rank_out = 0;
@@ -727,13 +732,19 @@ __global__ void __launch_bounds__(256) k_svd(const ExecCtx* __restrict__ px, con
   // (only for transposed sources, whose rows are M's columns; the planner
   // passes scratch copies that are not needed afterwards)
   double* S = ptrv(J.src, x);
-  const bool in_smem = (int64_t)(rows + 1) * cols <= smem_doubles || !J.trans;
+  const bool in_smem = fits || !J.trans;
   const int ldm = in_smem ? rows + 1 : J.lds;
   double* M = in_smem ? sm : S;  // column c at M + c*ldm
-  if (in_smem)
+  // (consecutive threads read consecutive source addresses)
+  if (in_smem && J.trans)
     for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-      int r = e / cols, c = e % cols;
-      M[c * ldm + r] = J.trans ? S[(int64_t)c * J.lds + r] : S[(int64_t)r * J.lds + c];
+      const int c = e / rows, r = e % rows;
+      M[c * ldm + r] = S[(int64_t)c * J.lds + r];
+    }
+  else if (in_smem)
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int r = e / cols, c = e % cols;
+      M[c * ldm + r] = S[(int64_t)r * J.lds + c];
     }
   if (threadIdx.x == 0) nrot = 0;
   for (int c = threadIdx.x; c < cols; c += blockDim.x) {
@@ -1072,7 +1083,6 @@ __global__ void k_finalize(const ExecCtx* __restrict__ px) {
 // ------------------------------------------------------------- launchers ----
 size_t norm_smem_bytes(int nmax) { return sizeof(double) * nmax * (nmax + 1); }
 size_t gemm_smem_bytes() { return sizeof(double) * gemm_smem_doubles(GT, GT); }
-size_t svd_smem_bytes(int rows, int cols) { return sizeof(double) * (size_t)(rows + 1) * cols; }
 
 static bool g_attr_done = false;
 
@@ -1092,7 +1102,7 @@ cudaError_t kernels_init() {
   e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_MAX_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           8 * (SVD_SMEM_MATRIX_DOUBLES + svd_colarr_doubles(SVD_MAXDIM)));
+                           8 * std::max(SVD_SMEM_DOUBLES, svd_colarr_doubles(SVD_MAXDIM)));
   if (e != cudaSuccess) return e;
   g_attr_done = true;
   return cudaSuccess;
@@ -1123,7 +1133,7 @@ static void launch_gemm(int mode, int cells, int count, size_t sm, cudaStream_t 
     launch_gemm_mode<GM_F64>(cells, count, sm, s, x, go, gt, mmax, nb);
 }
 
-void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t svd_smem, cudaStream_t s) {
+void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaStream_t s) {
   if (st.count <= 0) return;
   switch (st.kind) {
     case ST_GEMM:
@@ -1148,12 +1158,11 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t
       break;
     case ST_SVD:
       {
-      // st.aux = largest column count of the stage; st.smem covers its
-      // per-column arrays and the matrix area
+      // st.aux = largest column count of the stage; st.smem covers the
+      // per-column arrays of any job and the matrices that fit
       const int cmax = st.aux > 0 ? st.aux : SVD_MAXDIM;
-      const size_t sm = st.smem > 0 ? (size_t)st.smem : svd_smem + 8 * (size_t)svd_colarr_doubles(cmax);
-      k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first,
-                                      (int)(sm / 8) - svd_colarr_doubles(cmax), cmax);
+      const size_t sm = st.smem > 0 ? (size_t)st.smem : 8 * (size_t)SVD_SMEM_DOUBLES;
+      k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first, (int)(sm / 8), cmax);
     }
       break;
     case ST_NORM:

@@ -10,7 +10,11 @@ constexpr int SVD_MAXDIM = 256;  // largest Jacobi SVD (rows and columns)
 constexpr int NORM_MAXN = 128;   // largest matrix of a spectral-norm job
 constexpr int GEMM_AUX_FP32 = 1 << 24;  // Stage::aux flag of a GEMM stage: FP32 products and sums
 constexpr int GEMM_AUX_DF = 1 << 25;    // Stage::aux flag of a GEMM stage: compensated FP32 (double-float)
-constexpr int SVD_SMEM_MATRIX_DOUBLES = 129 * 64;  // SVD matrices up to this size sit in shared memory (66 KB)
+// Dynamic shared memory of an SVD launch at most (the per-column arrays of a
+// job, then its matrix when that fits).  76 KB: two CTAs on an SM, which
+// leaves ~90 KB of L1 to the matrices that stay in global memory; a 72 KB cap
+// (three CTAs, ~26 KB of L1) ran those 2.3x slower.
+constexpr int SVD_SMEM_DOUBLES = 9732;
 
 #ifdef __CUDACC__
 #define H2_HOST_DEVICE __host__ __device__
@@ -40,8 +44,7 @@ struct DeviceJobs {
 
 cudaError_t kernels_init();
 size_t gemm_smem_bytes();
-size_t svd_smem_bytes(int rows, int cols);
-void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, size_t svd_smem, cudaStream_t s);
+void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaStream_t s);
 void launch_finalize(const ExecCtx* x, int nrank, cudaStream_t s);
 
 }  // namespace h2

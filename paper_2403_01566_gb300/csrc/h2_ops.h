@@ -84,10 +84,13 @@ struct QrJob {
   Dim rows, cols;
   int keep;
   // Column pivoting (largest remaining column norm first) when piv is set:
-  // a P = Q R with P[:, j] = e_{piv[j]}; piv holds cols int32 (cols <= 128,
+  // a P = Q R with P[:, j] = e_{piv[j]}; piv holds cols int32 (cols <= 256,
   // else the factorisation is unpivoted and piv the identity).  Used where an
   // SVD of R^T follows: its one-sided Jacobi then needs about half the sweeps.
   Ptr piv;
+  // Layout of the R output (bits): 1 = columns back in the original order
+  // (R P^T, with pivoting); 2 = transposed (r[c * ldr + i] = R(i, c)).
+  int rmode;
 };
 
 // out(rows x ncols) = H_0 H_1 ... H_{q-1} [Y; 0]  with the reflectors of a QrJob

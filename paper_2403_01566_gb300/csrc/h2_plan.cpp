@@ -108,6 +108,7 @@ struct Builder {
   std::vector<QApplyJob> qa;
   std::vector<SvdJob> sv;
   int sv_maxr = 1, sv_maxc = 1;  // largest pending SVD job
+  int64_t sv_need = 0;           // shared memory (doubles) of the largest pending SVD job
   std::vector<double> sv_cost;   // static cost bound of each pending SVD job (from svd_size)
   std::vector<ScanJob> sc;
   std::vector<NormJob> nj;
@@ -194,8 +195,8 @@ struct Builder {
   // sizing of the stage); keep = 1 when a Q application needs the reflectors.
   int qr_smem = 0;
   void qr(Ptr a, int lda, Dim rows, Dim cols, Ptr tau, Ptr r, int ldr, int keep, int maxr, int maxc,
-          Ptr piv = NONE()) {
-    qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep, piv});
+          Ptr piv = NONE(), int rmode = 0) {
+    qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep, piv, rmode});
     qj_cost.push_back((double)maxr * maxc * maxc);
     const int64_t cap = 6144;  // doubles (48 KB)
     const int64_t need = (int64_t)maxr * maxc;
@@ -244,35 +245,31 @@ struct Builder {
     P.qap.insert(P.qap.end(), qa.begin(), qa.end());
     qa.clear();
   }
-  void svd(Ptr src, int lds, int trans, DimV rows, DimV cols, Ptr u, int ldu, Ptr sig, int mode, double tol,
-           int tol_idx, int rank_slot, int cap, int norm_idx) {
-    if (rows.max > SVD_MAXDIM || cols.max > SVD_MAXDIM) throw std::runtime_error("svd too large");
-    svd_size(rows.max, cols.max);
-    sv.push_back(SvdJob{src, u, sig, lds, ldu, rows.d(), cols.d(), trans, mode, tol, tol_idx, rank_slot, cap,
-                        norm_idx, NONE()});
-  }
   void svd_size(int rows, int cols) {
+    if (rows > SVD_MAXDIM || cols > SVD_MAXDIM) throw std::runtime_error("svd too large");
     sv_cost.push_back((double)rows * cols * cols);
+    sv_need = std::max<int64_t>(sv_need, svd_colarr_doubles(cols) + (int64_t)(rows + 1) * cols);
     sv_maxr = std::max(sv_maxr, rows);
     sv_maxc = std::max(sv_maxc, cols);
     P.svd_maxrows = std::max(P.svd_maxrows, rows);
     P.svd_maxcols = std::max(P.svd_maxcols, cols);
   }
-  // One launch per stage: shared memory for the largest job, capped at 129 x 64
-  // doubles (66 KB, three CTAs per SM); larger jobs run in place in global
-  // memory.  (A separate one-CTA-per-SM launch for the large jobs measured no
-  // faster: it serialises behind the small ones.)
+  // One launch per stage: shared memory for the largest job (its per-column
+  // arrays and matrix), capped at SVD_SMEM_DOUBLES; the matrices of larger
+  // jobs run in place in global memory.  (A separate
+  // one-CTA-per-SM launch for the large jobs measured no faster: it
+  // serialises behind the small ones.)
   void flush_svd(int tag) {
     if (sv.empty()) return;
-    const int smem = (int)(sizeof(double) *
-                           (std::min<int64_t>((int64_t)(sv_maxr + 1) * sv_maxc, SVD_SMEM_MATRIX_DOUBLES) +
-                            svd_colarr_doubles(sv_maxc)));
+    const int smem = (int)(sizeof(double) * std::max<int64_t>(svd_colarr_doubles(sv_maxc),
+                                                              std::min<int64_t>(sv_need, SVD_SMEM_DOUBLES)));
     largest_first(sv, sv_cost);
     P.stages.push_back(Stage{ST_SVD, (int64_t)P.svd.size(), (int)sv.size(), tag, smem, sv_maxc});
     P.svd.insert(P.svd.end(), sv.begin(), sv.end());
     sv.clear();
     sv_cost.clear();
     sv_maxr = sv_maxc = 1;
+    sv_need = 0;
   }
   int nj_nmax = 1;  // largest n of the pending norm jobs
   void norm(Ptr src, int lds, DimV n, int norm_idx) {
@@ -1044,6 +1041,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       const int64_t mark = B.ws;
       struct Scr {
         int64_t W1, W2, tau1, tau2, rho1, rho2, Gc, Wc, tauc, rhoc, U, sig, piv;
+        bool two_step;            // SVD through a second QR (M too tall for shared memory)
+        int64_t tau2c, R2, Y;     // its reflector scalars, triangle and small singular vectors
         int qc_max;
       };
       std::vector<Scr> scr(jobs.size());
@@ -1083,6 +1082,21 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         s.U = B.alloc((int64_t)(m1 + m2) * AGGC);
         s.sig = B.alloc(m1 + m2);
         s.piv = B.alloc((m1 + m2 + 1) / 2);  // int32 pivot order of the condensed QR
+        {
+          // M = rho_c^T is (m1+m2) x q; when it does not fit the SVD's shared
+          // memory and is taller than wide, the SVD runs on the triangle R2 of
+          // M = Q2 R2 instead: same Gram matrix, hence the same rotations and
+          // singular values, with q-long columns; U = Q2 Y afterwards
+          const int gr = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
+          const int qmax = std::min(m1 + m2, gr);
+          s.two_step = svd_colarr_doubles(qmax) + (int64_t)(m1 + m2 + 1) * qmax > SVD_SMEM_DOUBLES && m1 + m2 > qmax;
+          if (s.two_step) {
+            ++P.stats["agg_two_step"];
+            s.tau2c = B.alloc(qmax);
+            s.R2 = B.alloc((int64_t)qmax * qmax);
+            s.Y = B.alloc((int64_t)qmax * AGGC);
+          }
+        }
         if (m1 + m2 > AGGC) throw std::runtime_error("agglomeration width");
       }
       B.flush_copy(TAG_AGG);
@@ -1139,8 +1153,26 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         const int m1 = J.f1.m.max, m2 = J.f2.m.max;
         const int rows = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
         const Dim wd = merged_width(J.f1.m, J.f2.m);
+        // two-step jobs take R with its columns back in the original order
+        // (R P^T): then M = (R P^T)^T carries the pivot and U needs no permutation
         B.qr(PT(AR_WS, s.Wc), rows, DC(rows), wd, PT(AR_WS, s.tauc), PT(AR_WS, s.rhoc), AGGC, 0, rows,
-             J.f1.m.max + J.f2.m.max, PT(AR_WS, s.piv));
+             J.f1.m.max + J.f2.m.max, PT(AR_WS, s.piv), s.two_step ? 1 : 0);
+      }
+      B.flush_qr(TAG_AGG);
+      // second QR of the two-step jobs: M = rho_c^T = Q2 R2 (in place, the
+      // reflectors stay for U = Q2 Y; R2 stored transposed for the SVD)
+      for (size_t j = 0; j < jobs.size(); ++j) {
+        const MergeJob& J = jobs[j];
+        Scr& s = scr[j];
+        if (!s.two_step) continue;
+        const int m1 = J.f1.m.max, m2 = J.f2.m.max;
+        const int gr = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
+        const int qmax = std::min(m1 + m2, gr);
+        const Dim wd = merged_width(J.f1.m, J.f2.m);
+        Dim qcols = wd;
+        qcols.mc = gr;
+        B.qr(PT(AR_WS, s.rhoc), AGGC, wd, qcols, PT(AR_WS, s.tau2c), PT(AR_WS, s.R2), qmax, 1, m1 + m2, qmax, NONE(),
+             2);
       }
       B.flush_qr(TAG_AGG);
       for (size_t j = 0; j < jobs.size(); ++j) {
@@ -1155,11 +1187,31 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         const int gc_rows = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
         Dim qcols = wd;
         qcols.mc = gc_rows;
+        if (s.two_step) {
+          const int qmax = std::min(m1 + m2, gc_rows);
+          B.svd_size(qmax, qmax);
+          B.sv.push_back(SvdJob{PT(AR_WS, s.R2), PT(AR_WS, s.Y), PT(AR_WS, s.sig), qmax, AGGC, qcols, qcols, 1, 2, J.rel,
+                                PARAM_TOL_AGG, outs[j].m.s, AGGM, -1, NONE()});
+          continue;
+        }
         B.svd_size(m1 + m2, std::min(m1 + m2, gc_rows));
         B.sv.push_back(SvdJob{PT(AR_WS, s.rhoc), PT(AR_WS, s.U), PT(AR_WS, s.sig), AGGC, AGGC, wd, qcols, 1, 2, J.rel,
                               PARAM_TOL_AGG, outs[j].m.s, AGGM, -1, PT(AR_WS, s.piv)});
       }
       B.flush_svd(TAG_AGG);
+      // two-step jobs: U[:, :k'] = Q2 [Y[:, :k']; 0]
+      for (size_t j = 0; j < jobs.size(); ++j) {
+        const MergeJob& J = jobs[j];
+        Scr& s = scr[j];
+        if (!s.two_step) continue;
+        const int gr = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
+        const Dim wd = merged_width(J.f1.m, J.f2.m);
+        Dim qcols = wd;
+        qcols.mc = gr;
+        B.qapply(PT(AR_WS, s.rhoc), AGGC, PT(AR_WS, s.tau2c), wd, qcols, PT(AR_WS, s.Y), AGGC, outs[j].m.d(),
+                 PT(AR_WS, s.U), AGGC);
+      }
+      B.flush_qapply(TAG_AGG);
       for (size_t j = 0; j < jobs.size(); ++j) {
         const MergeJob& J = jobs[j];
         Scr& s = scr[j];

@@ -168,8 +168,12 @@ struct Interp {
     double* r = ptr(J.r);
     if (r)
       for (int i = 0; i < cols; ++i)
-        for (int c = 0; c < cols; ++c)
-          r[(int64_t)i * J.ldr + c] = (c >= i && i < q) ? a[(int64_t)c * lda + i] : 0.0;
+        for (int c = 0; c < cols; ++c) {
+          const double v = (c >= i && i < q) ? a[(int64_t)c * lda + i] : 0.0;
+          const int dc = ((J.rmode & 1) && piv) ? piv[c] : c;  // R P^T: original column order
+          if (J.rmode & 2) r[(int64_t)dc * J.ldr + i] = v;      // transposed store
+          else r[(int64_t)i * J.ldr + dc] = v;
+        }
   }
 
   void qapply(const QApplyJob& J) {
@@ -398,6 +402,7 @@ int main(int argc, char** argv) {
   mo.hmatrix = hmatrix;
   auto P = make_product_plan(dX, dY, mo);
 
+  for (const auto& kv : P->stats) std::printf("stat %s %lld\n", kv.first.c_str(), (long long)kv.second);
   Interp E;
   std::vector<double> ws(std::max<int64_t>(P->ws_len, 1), std::nan("")), fac(std::max<int64_t>(P->fac_len, 1), std::nan(""));
   std::vector<double> arC(std::max<int64_t>(P->c_len, 1), 0.0), kon(P->konst);

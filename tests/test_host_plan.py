@@ -52,7 +52,8 @@ def run_interpreter(exe, w, eps, tmp_path, hmatrix=False, max_rank=0):
     n = w.n
     D = np.frombuffer(raw[:8 * n * n].tobytes(), dtype=np.float64).reshape(n, n)
     ranks = np.frombuffer(raw[8 * n * n:].tobytes(), dtype=np.int32)
-    return D, ranks
+    stats = {ln.split()[1]: int(ln.split()[2]) for ln in r.stdout.splitlines() if ln.startswith("stat ")}
+    return D, ranks, stats
 
 
 def worst_blockrel(D, Dref, Z, blocks):
@@ -69,12 +70,17 @@ CASES = [
     (I.plain_1d(1000), 1e-4),                     # ragged leaves
     (I.square_2d(1500, seed=7, leaf=32, order=3), 1e-6),
     (I.cube_3d(1200, seed=11, leaf=40, order=2), 1e-4),
+    # k = 64: the widest agglomeration merges exceed the SVD's shared memory
+    # and take the second-QR route
+    (I.cube_3d(1500, seed=5, leaf=48, order=4), 1e-6),
 ]
 
 
 @pytest.mark.parametrize("w,eps", CASES, ids=[f"{w.name}-{e:g}" for w, e in CASES])
 def test_planned_stages_reproduce_the_oracle(interpreter, tmp_path, w, eps):
-    D, ranks = run_interpreter(interpreter, w, eps, tmp_path)
+    D, ranks, stats = run_interpreter(interpreter, w, eps, tmp_path)
+    if w.dim == 3 and w.order == 4:
+        assert stats.get("agg_two_step", 0) > 0
     X, Y = build_pair(w)
     res = O.multiply(X, Y, eps)
     Z = X.dense() @ Y.dense()
@@ -86,7 +92,7 @@ def test_planned_stages_reproduce_the_oracle(interpreter, tmp_path, w, eps):
 
 def test_planned_hmatrix_variant_reproduces_the_oracle_factors(interpreter, tmp_path):
     w = I.grid_2d(32)
-    D, _ = run_interpreter(interpreter, w, 1e-6, tmp_path, hmatrix=True)
+    D, _, _ = run_interpreter(interpreter, w, 1e-6, tmp_path, hmatrix=True)
     X, Y = build_pair(w)
     res = O.multiply(X, Y, 1e-6)
     Do = res.C.dense()
