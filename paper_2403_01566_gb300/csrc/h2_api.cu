@@ -333,7 +333,13 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
         case ST_QR: {
           const QrJob& Q = P.qr[J];
           const double r = dv(Q.rows), c = dv(Q.cols);
-          fl += r >= c ? 2 * r * c * c - 2 * c * c * c / 3 : 2 * c * r * r - 2 * r * r * r / 3;
+          if (Q.rank_slot >= 0) {
+            // j = 0..k-1 Householder steps on (r - j) x (c - j) trailing parts
+            const double k = slot[Q.rank_slot];
+            fl += 4 * k * r * c - 2 * k * k * (r + c) + 4 * k * k * k / 3;
+          } else {
+            fl += r >= c ? 2 * r * c * c - 2 * c * c * c / 3 : 2 * c * r * r - 2 * r * r * r / 3;
+          }
           by += 16 * r * c;
           break;
         }

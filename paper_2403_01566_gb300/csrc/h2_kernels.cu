@@ -332,11 +332,16 @@ constexpr int QR_MAXPIV = 256;  // largest column count of a pivoted QR
 // Each step: warp 0 alone picks the pivot, swaps, forms the reflector and
 // scales it (no block barrier inside), then all warps update the trailing
 // columns; two block barriers per step.
-__device__ void householder_cols(double* a, int lda, int rows, int cols, double* tau, double* sh, int* piv,
-                                 double* cn, double* cn0) {
+//
+// With pivoting and floor2 > 0 the factorisation stops at the first step j
+// whose trailing columns hold a squared Frobenius norm (the sum of cn) <=
+// floor2 * ||a||_F^2; tau[j..] is then 0.  Returns the number of steps taken.
+__device__ int householder_cols(double* a, int lda, int rows, int cols, double* tau, double* sh, int* piv,
+                                double* cn, double* cn0, double floor2 = -1.0) {
   const int q = min(rows, cols);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   constexpr double kRecompute = 1.4901161193847656e-08;  // 2^-26
+  double thr = -1.0;  // truncation threshold (warp 0)
   if (piv) {
     for (int c = threadIdx.x; c < cols; c += blockDim.x) piv[c] = c;
     for (int c = warp; c < cols; c += nwarp) {
@@ -347,18 +352,27 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
       if (lane == 0) cn[c] = cn0[c] = s;
     }
     __syncthreads();
+    if (floor2 > 0.0 && warp == 0) {
+      double s = 0.0;
+      for (int c = lane; c < cols; c += 32) s += cn[c];
+      thr = floor2 * warp_sum(s);
+    }
   }
+  int steps = q;
   for (int j = 0; j < q; ++j) {
     double* col = a + (int64_t)j * lda;
     if (warp == 0) {
+      bool stop = false;
       if (piv) {
-        double bv = -1.0;
+        double bv = -1.0, rs = 0.0;
         int bi = j;
-        for (int c = j + lane; c < cols; c += 32)
+        for (int c = j + lane; c < cols; c += 32) {
+          rs += cn[c];
           if (cn[c] > bv) {
             bv = cn[c];
             bi = c;
           }
+        }
         for (int o = 16; o > 0; o >>= 1) {
           const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -367,7 +381,8 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
             bi = oi;
           }
         }
-        if (bi != j) {
+        if (thr >= 0.0) stop = warp_sum(rs) <= thr;  // the same sum in every lane
+        if (!stop && bi != j) {
           double* cp = a + (int64_t)bi * lda;
           for (int i = lane; i < rows; i += 32) {
             const double t = col[i];
@@ -388,24 +403,32 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
           __syncwarp();
         }
       }
-      double s2 = 0.0;
-      for (int i = j + 1 + lane; i < rows; i += 32) s2 = fma(col[i], col[i], s2);
-      s2 = warp_sum(s2);
-      const double alpha = col[j];
-      double t = 0.0, sc = 0.0;
-      if (s2 > 0.0) {
-        double beta;
-        householder_scalars(alpha, s2, beta, t, sc);
-        for (int i = j + 1 + lane; i < rows; i += 32) col[i] *= sc;
-        __syncwarp();
-        if (lane == 0) col[j] = beta;
+      double t = 0.0;
+      if (!stop) {
+        double s2 = 0.0;
+        for (int i = j + 1 + lane; i < rows; i += 32) s2 = fma(col[i], col[i], s2);
+        s2 = warp_sum(s2);
+        const double alpha = col[j];
+        double sc = 0.0;
+        if (s2 > 0.0) {
+          double beta;
+          householder_scalars(alpha, s2, beta, t, sc);
+          for (int i = j + 1 + lane; i < rows; i += 32) col[i] *= sc;
+          __syncwarp();
+          if (lane == 0) col[j] = beta;
+        }
       }
       if (lane == 0) {
         sh[0] = t;
+        sh[1] = stop ? 1.0 : 0.0;
         if (tau) tau[j] = t;
       }
     }
     __syncthreads();
+    if (sh[1] != 0.0) {
+      steps = j;
+      break;
+    }
     const double t = sh[0];
     if (t != 0.0) {
       // trailing columns: teams of ts lanes per column (short columns use small
@@ -459,6 +482,9 @@ __device__ void householder_cols(double* a, int lda, int rows, int cols, double*
     }
     __syncthreads();
   }
+  if (tau)
+    for (int c = steps + threadIdx.x; c < q; c += blockDim.x) tau[c] = 0.0;
+  return steps;
 }
 
 // R factor of a tall column-major matrix a (rows x cols) without its Q:
@@ -561,10 +587,14 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
   }
   const int lda = J.lda;
   const int q = min(rows, cols);
+  // truncation at a noise floor (pivoted factorisations only)
+  const double floor2 = (piv && J.trunc_idx >= 0) ? x.scal[J.trunc_idx] : -1.0;
+  int* rank_out = J.rank_slot >= 0 ? x.slot + J.rank_slot : nullptr;
   if (rows <= 0 || cols <= 0) {
     if (r) write_r(J, r, nullptr, 0, cols, 0, nullptr);
     if (piv)
       for (int c = threadIdx.x; c < cols; c += blockDim.x) piv[c] = c;
+    if (rank_out && threadIdx.x == 0) *rank_out = 0;
     return;
   }
   if ((int64_t)rows * cols <= smem_doubles) {
@@ -574,13 +604,14 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
       sm[e] = a[(int64_t)c * lda + i];
     }
     __syncthreads();
-    householder_cols(sm, rows, rows, cols, tau, sh, piv, cn, cn0);
+    const int rk = householder_cols(sm, rows, rows, cols, tau, sh, piv, cn, cn0, floor2);
     if (J.keep)
       for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
         const int c = (int)(e / rows), i = (int)(e % rows);
         a[(int64_t)c * lda + i] = sm[e];
       }
-    if (r) write_r(J, r, sm, rows, cols, q, piv);
+    if (r) write_r(J, r, sm, rows, cols, rk, piv);
+    if (rank_out && threadIdx.x == 0) *rank_out = rk;
     return;
   }
   if (!J.keep && cols <= QR_TSQR_MAXC && smem_doubles / cols - cols >= 16) {
@@ -589,15 +620,18 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
     // follows an R-only job)
     const int ld = smem_doubles / cols;
     tsqr_r(a, lda, rows, cols, sm, ld, ld - cols, sh);
-    if (piv) householder_cols(sm, ld, cols, cols, nullptr, sh, piv, cn, cn0);
+    // the triangle has the Frobenius norm of a: the same truncation applies
+    const int rk = piv ? householder_cols(sm, ld, cols, cols, nullptr, sh, piv, cn, cn0, floor2) : q;
     if (tau)
       for (int c = threadIdx.x; c < q; c += blockDim.x) tau[c] = 0.0;
-    if (r) write_r(J, r, sm, ld, cols, q, piv);
+    if (r) write_r(J, r, sm, ld, cols, rk, piv);
+    if (rank_out && threadIdx.x == 0) *rank_out = rk;
     return;
   }
   // general case: in place in global memory
-  householder_cols(a, lda, rows, cols, tau, sh, piv, cn, cn0);
-  if (r) write_r(J, r, a, lda, cols, q, piv);
+  const int rk = householder_cols(a, lda, rows, cols, tau, sh, piv, cn, cn0, floor2);
+  if (r) write_r(J, r, a, lda, cols, rk, piv);
+  if (rank_out && threadIdx.x == 0) *rank_out = rk;
 }
 
 // out = H_0 ... H_{q-1} [Y; 0].  Threads: column c = tid % nc of out, row

@@ -91,6 +91,13 @@ struct QrJob {
   // Layout of the R output (bits): 1 = columns back in the original order
   // (R P^T, with pivoting); 2 = transposed (r[c * ldr + i] = R(i, c)).
   int rmode;
+  // Truncation of a pivoted QR at a noise floor (trunc_idx >= 0): the
+  // factorisation stops at the first step j whose trailing columns hold a
+  // squared Frobenius norm <= scal[trunc_idx] * ||a||_F^2; R keeps rows < j
+  // (the rest zero), tau[j..] = 0, and j is written to slot[rank_slot]
+  // (rank_slot >= 0; min(rows, cols) when the QR runs to the end).
+  int trunc_idx;
+  int rank_slot;
 };
 
 // out(rows x ncols) = H_0 H_1 ... H_{q-1} [Y; 0]  with the reflectors of a QrJob

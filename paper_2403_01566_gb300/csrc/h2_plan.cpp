@@ -195,8 +195,8 @@ struct Builder {
   // sizing of the stage); keep = 1 when a Q application needs the reflectors.
   int qr_smem = 0;
   void qr(Ptr a, int lda, Dim rows, Dim cols, Ptr tau, Ptr r, int ldr, int keep, int maxr, int maxc,
-          Ptr piv = NONE(), int rmode = 0) {
-    qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep, piv, rmode});
+          Ptr piv = NONE(), int rmode = 0, int trunc_idx = -1, int rank_slot = -1) {
+    qj.push_back(QrJob{a, tau, r, lda, ldr, rows, cols, keep, piv, rmode, trunc_idx, rank_slot});
     qj_cost.push_back((double)maxr * maxc * maxc);
     const int64_t cap = 6144;  // doubles (48 KB)
     const int64_t need = (int64_t)maxr * maxc;
@@ -1043,6 +1043,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         int64_t W1, W2, tau1, tau2, rho1, rho2, Gc, Wc, tauc, rhoc, U, sig, piv;
         bool two_step;            // SVD through a second QR (M too tall for shared memory)
         int64_t tau2c, R2, Y;     // its reflector scalars, triangle and small singular vectors
+        int rslot;                // rows of rho_c kept above the noise floor (slot)
         int qc_max;
       };
       std::vector<Scr> scr(jobs.size());
@@ -1083,13 +1084,16 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         s.sig = B.alloc(m1 + m2);
         s.piv = B.alloc((m1 + m2 + 1) / 2);  // int32 pivot order of the condensed QR
         {
-          // M = rho_c^T is (m1+m2) x q; when it does not fit the SVD's shared
-          // memory and is taller than wide, the SVD runs on the triangle R2 of
-          // M = Q2 R2 instead: same Gram matrix, hence the same rotations and
-          // singular values, with q-long columns; U = Q2 Y afterwards
+          // The pivoted QR of Gc stops at the SVD's noise floor: rho_c keeps
+          // its first r rows, r at run time.  M = rho_c^T is (m1+m2) x r; when
+          // it may not fit the SVD's shared memory, the SVD runs on the
+          // triangle R2 of M = Q2 R2 instead: same Gram matrix, hence the same
+          // rotations and singular values, with r-long columns; U = Q2 Y
+          // afterwards
           const int gr = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
           const int qmax = std::min(m1 + m2, gr);
-          s.two_step = svd_colarr_doubles(qmax) + (int64_t)(m1 + m2 + 1) * qmax > SVD_SMEM_DOUBLES && m1 + m2 > qmax;
+          s.rslot = B.slot(0);
+          s.two_step = svd_colarr_doubles(qmax) + (int64_t)(m1 + m2 + 1) * qmax > SVD_SMEM_DOUBLES;
           if (s.two_step) {
             ++P.stats["agg_two_step"];
             s.tau2c = B.alloc(qmax);
@@ -1156,7 +1160,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         // two-step jobs take R with its columns back in the original order
         // (R P^T): then M = (R P^T)^T carries the pivot and U needs no permutation
         B.qr(PT(AR_WS, s.Wc), rows, DC(rows), wd, PT(AR_WS, s.tauc), PT(AR_WS, s.rhoc), AGGC, 0, rows,
-             J.f1.m.max + J.f2.m.max, PT(AR_WS, s.piv), s.two_step ? 1 : 0);
+             J.f1.m.max + J.f2.m.max, PT(AR_WS, s.piv), s.two_step ? 1 : 0, PARAM_SVD_FLOOR, s.rslot);
       }
       B.flush_qr(TAG_AGG);
       // second QR of the two-step jobs: M = rho_c^T = Q2 R2 (in place, the
@@ -1169,10 +1173,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         const int gr = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
         const int qmax = std::min(m1 + m2, gr);
         const Dim wd = merged_width(J.f1.m, J.f2.m);
-        Dim qcols = wd;
-        qcols.mc = gr;
-        B.qr(PT(AR_WS, s.rhoc), AGGC, wd, qcols, PT(AR_WS, s.tau2c), PT(AR_WS, s.R2), qmax, 1, m1 + m2, qmax, NONE(),
-             2);
+        B.qr(PT(AR_WS, s.rhoc), AGGC, wd, DS(s.rslot, 0), PT(AR_WS, s.tau2c), PT(AR_WS, s.R2), qmax, 1, m1 + m2, qmax,
+             NONE(), 2);
       }
       B.flush_qr(TAG_AGG);
       for (size_t j = 0; j < jobs.size(); ++j) {
@@ -1182,11 +1184,10 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         // M = rho_c^T ((m1+m2) x (m1+m2)); rows and cols are the merged width
         const Dim wd = merged_width(J.f1.m, J.f2.m);
         if (m1 + m2 > SVD_MAXDIM) throw std::runtime_error("agglomeration svd too large");
-        // M = rho_c^T (width x q), q = min(width, rows of Gc): the rows of rho_c
-        // beyond q are zero
+        // M = rho_c^T (width x r), r <= min(width, rows of Gc) the rows of
+        // rho_c above the noise floor (the rest is zero)
         const int gc_rows = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
-        Dim qcols = wd;
-        qcols.mc = gc_rows;
+        const Dim qcols = DS(s.rslot, 0);
         if (s.two_step) {
           const int qmax = std::min(m1 + m2, gc_rows);
           B.svd_size(qmax, qmax);
@@ -1204,12 +1205,9 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         const MergeJob& J = jobs[j];
         Scr& s = scr[j];
         if (!s.two_step) continue;
-        const int gr = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
         const Dim wd = merged_width(J.f1.m, J.f2.m);
-        Dim qcols = wd;
-        qcols.mc = gr;
-        B.qapply(PT(AR_WS, s.rhoc), AGGC, PT(AR_WS, s.tau2c), wd, qcols, PT(AR_WS, s.Y), AGGC, outs[j].m.d(),
-                 PT(AR_WS, s.U), AGGC);
+        B.qapply(PT(AR_WS, s.rhoc), AGGC, PT(AR_WS, s.tau2c), wd, DS(s.rslot, 0), PT(AR_WS, s.Y), AGGC,
+                 outs[j].m.d(), PT(AR_WS, s.U), AGGC);
       }
       B.flush_qapply(TAG_AGG);
       for (size_t j = 0; j < jobs.size(); ++j) {

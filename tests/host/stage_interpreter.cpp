@@ -117,26 +117,45 @@ struct Interp {
   }
 
   // Householder QR of the column-major rows x cols matrix, with the column
-  // pivoting (largest remaining norm first) when the job asks for it.
+  // pivoting (largest remaining norm first) when the job asks for it, and the
+  // pivoted factorisation stopped once the trailing columns fall below the
+  // job's noise floor (squared Frobenius norm <= floor * ||a||_F^2).
+  long qr_truncated = 0;  // pivoted QRs stopped at the noise floor
   void qr(const QrJob& J) {
     const int rows = dimv(J.rows), cols = dimv(J.cols);
     double* a = ptr(J.a);
     double* tau = ptr(J.tau);
-    const int lda = J.lda, q = std::min(rows, cols);
+    const int lda = J.lda;
+    int q = std::min(std::max(rows, 0), std::max(cols, 0));
     int* piv = reinterpret_cast<int*>(ptr(J.piv));
     if (piv)
       for (int c = 0; c < cols; ++c) piv[c] = c;
+    double thr = -1.0;
+    if (piv && J.trunc_idx >= 0) {
+      double fro = 0.0;
+      for (int c = 0; c < cols; ++c)
+        for (int i = 0; i < rows; ++i) fro += a[(int64_t)c * lda + i] * a[(int64_t)c * lda + i];
+      thr = scal[J.trunc_idx] * fro;
+    }
     for (int j = 0; j < q; ++j) {
       if (piv) {
         int p = j;
-        double best = -1.0;
+        double best = -1.0, rest = 0.0;
         for (int c = j; c < cols; ++c) {
           double s2 = 0.0;
           for (int i = j; i < rows; ++i) s2 += a[(int64_t)c * lda + i] * a[(int64_t)c * lda + i];
+          rest += s2;
           if (s2 > best) {
             best = s2;
             p = c;
           }
+        }
+        if (thr >= 0.0 && rest <= thr) {
+          ++qr_truncated;
+          for (int c = j; c < q; ++c)
+            if (tau) tau[c] = 0.0;
+          q = j;
+          break;
         }
         if (p != j) {
           for (int i = 0; i < rows; ++i) std::swap(a[(int64_t)j * lda + i], a[(int64_t)p * lda + i]);
@@ -165,6 +184,7 @@ struct Interp {
       }
       if (tau) tau[j] = t;
     }
+    if (J.rank_slot >= 0) slot[J.rank_slot] = q;
     double* r = ptr(J.r);
     if (r)
       for (int i = 0; i < cols; ++i)
@@ -198,8 +218,8 @@ struct Interp {
     }
   }
 
-  // Cyclic one-sided Jacobi on M (rows x cols); columns below 2^-50 ||M||_F
-  // count as zero.  Writes sigma (sorted), U (rows permuted by the job's
+  // Cyclic one-sided Jacobi on M (rows x cols); columns below the noise floor
+  // (sqrt(scal[PARAM_SVD_FLOOR]) ||M||_F) count as zero.  Writes sigma (sorted), U (rows permuted by the job's
   // pivot order) and the rank of the job's truncation mode.
   void svd(const SvdJob& J) {
     const int rows = dimv(J.rows), cols = dimv(J.cols);
@@ -216,7 +236,7 @@ struct Interp {
         M[(size_t)c * rows + r] = J.trans ? S[(int64_t)c * J.lds + r] : S[(int64_t)r * J.lds + c];
     double fro = 0.0;
     for (double v : M) fro += v * v;
-    const double tiny2 = fro * 7.888609052210118e-31;  // 2^-100
+    const double tiny2 = fro * scal[PARAM_SVD_FLOOR];
     bool converged = false;
     for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
       converged = true;
@@ -418,11 +438,16 @@ int main(int argc, char** argv) {
   E.idx = P->idx;
   E.scal[PARAM_TOL_BASIS] = eps / 4.0 * std::sqrt(1.0 - 2.0 * 0.25);
   E.scal[PARAM_TOL_AGG] = eps / 3.0;
+  // noise floor of the FP64 form: eps 2^-20 within [2^-50, 2^-40], squared
+  const double fl = eps > 0.0 ? std::min(std::ldexp(1.0, -40), std::max(std::ldexp(1.0, -50), eps * std::ldexp(1.0, -20)))
+                              : std::ldexp(1.0, -50);
+  E.scal[PARAM_SVD_FLOOR] = fl * fl;
   E.run(*P);
   if (E.err != 0) {
     std::fprintf(stderr, "interpreter error %d\n", E.err);
     return 4;
   }
+  std::printf("stat qr_truncated %ld\n", E.qr_truncated);
 
   // dense expansion in the caller's ordering
   const BlockTree& BC = *P->cblocks;
