@@ -115,13 +115,55 @@ struct GemmPol<GM_DF> {
   __device__ static double value(const A& a) { return (double)a.s + (double)a.c; }
 };
 
+// Outputs of this thread in an m x n tile: column c, rows r0 + q * rstep for
+// q < nv, where rstep = 256 / n rows are covered per step (threads beyond
+// rstep * n idle).  Every output of a thread shares its column, so one staged
+// B value serves all of its accumulators, and the Q accumulation chains are
+// independent (they interleave in the inner loop).  Requires
+// ceil(m / rstep) <= Q.
+struct OutMap {
+  int r0, c, rstep, nv;
+};
+__device__ __forceinline__ OutMap out_map(int m, int n) {
+  OutMap o;
+  o.rstep = 256 / n;
+  o.c = threadIdx.x % n;
+  o.r0 = threadIdx.x / n;
+  o.nv = (o.r0 < o.rstep && o.r0 < m) ? (m - o.r0 + o.rstep - 1) / o.rstep : 0;
+  return o;
+}
+
+// acc[q] += sum_l a[q * astep + l] b[l * ldb] (l < kc) for q < nv.  FP64
+// issue is the bound in the FP64 mode, so one output at a time; the FP32 and
+// compensated modes run four independent chains per pass to cover the latency
+// of their dependent FP32 steps.
+template <int Q, int MODE>
+__device__ __forceinline__ void mac_rows(typename GemmPol<MODE>::A (&acc)[Q], int nv,
+                                         const typename GemmPol<MODE>::S* a, int astep,
+                                         const typename GemmPol<MODE>::S* b, int ldb, int kc) {
+  using P = GemmPol<MODE>;
+  constexpr int CH = MODE == GM_F64 ? 1 : 4;
+#pragma unroll
+  for (int q0 = 0; q0 < Q; q0 += CH)
+    if (q0 < nv)
+      for (int l = 0; l < kc; ++l) {
+        const typename P::S bv = b[l * ldb];
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+          if (q0 + u < Q && q0 + u < nv) P::fma_acc(acc[q0 + u], a[(q0 + u) * astep + l], bv);
+      }
+}
+
 // acc[q] += op(A)(m x k) op(B)(k x n) for the outputs of this thread
 template <int Q, int MODE>
-__device__ __forceinline__ void gemm_accumulate(typename GemmPol<MODE>::A (&acc)[Q], int nq, int m, int n, int k,
-                                                const double* A, int lda, int ta, const double* B, int ldb, int tb,
-                                                typename GemmPol<MODE>::S* As, typename GemmPol<MODE>::S* Bs,
+__device__ __forceinline__ void gemm_accumulate(typename GemmPol<MODE>::A (&acc)[Q], const OutMap& om, int m, int n,
+                                                int k, const double* A, int lda, int ta, const double* B, int ldb,
+                                                int tb, typename GemmPol<MODE>::S* As, typename GemmPol<MODE>::S* Bs,
                                                 int ldbs) {
   using P = GemmPol<MODE>;
+  using S = typename P::S;
+  const S* ar = As + om.r0 * (GK + 1);
+  const int astep = om.rstep * (GK + 1);
   for (int kk = 0; kk < k; kk += GK) {
     const int kc = min(GK, k - kk);
     for (int e = threadIdx.x; e < m * kc; e += 256) {
@@ -133,18 +175,7 @@ __device__ __forceinline__ void gemm_accumulate(typename GemmPol<MODE>::A (&acc)
       Bs[l * ldbs + c] = P::stage(ld_op(B, ldb, tb, kk + l, c));
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      if (q < nq) {
-        const int e = threadIdx.x + 256 * q;
-        if (e < m * n) {
-          const int r = e / n, c = e % n;
-          typename P::A a = acc[q];
-          for (int l = 0; l < kc; ++l) P::fma_acc(a, As[r * (GK + 1) + l], Bs[l * ldbs + c]);
-          acc[q] = a;
-        }
-      }
-    }
+    mac_rows<Q, MODE>(acc, om.nv, ar, astep, Bs + om.c, ldbs, kc);
     __syncthreads();
   }
 }
@@ -158,10 +189,11 @@ __host__ __device__ constexpr int gemm_smem_doubles(int mmax, int nb) {
   return mmax * (GK + 1) + (GK + mmax) * (nb + 1);
 }
 
-// Q = outputs per thread (m * n <= 256 Q): small stages take a small Q, so
-// fewer registers and more resident CTAs per SM.  MODE = compute mode (above).
+// Q = outputs per thread (ceil(m / (256 / n)) <= Q, see out_map): small
+// stages take a small Q, so fewer registers and more resident CTAs per SM.
+// MODE = compute mode (above).
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs,
+__global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs,
                                               const GemmTerm* __restrict__ terms, int mmax, int nb) {
   using P = GemmPol<MODE>;
   using S = typename P::S;
@@ -176,11 +208,12 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
   const int m = dimv(O.m, x.slot);
   const int n = O.clampn ? min(dimv(O.n, x.slot), GT) : dimv(O.n, x.slot);
   if (m <= 0 || n <= 0) return;
-  if (m > mmax || n > nb || m * n > 256 * Q) {
+  auto fits = [&](int cols) { return (m + 256 / cols - 1) / (256 / cols) <= Q; };
+  if (m > mmax || n > nb || !fits(n)) {
     if (threadIdx.x == 0) set_err(x, -9);
     return;
   }
-  const int nq = (m * n + 255) / 256;
+  const OutMap om = out_map(m, n);
   double acc[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) acc[q] = 0.0;
@@ -194,10 +227,8 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
     const double* C = ptrv(Tm.c, x);
     if (B == nullptr) {  // plain add of op(A) (m x n)
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int e = threadIdx.x + 256 * q;
-        if (q < nq && e < m * n) acc[q] = fma(alpha, ld_op(A, Tm.lda, Tm.ta, e / n, e % n), acc[q]);
-      }
+      for (int q = 0; q < Q; ++q)
+        if (q < om.nv) acc[q] = fma(alpha, ld_op(A, Tm.lda, Tm.ta, om.r0 + q * om.rstep, om.c), acc[q]);
       continue;
     }
     const int k1 = dimv(Tm.k1, x.slot);
@@ -205,28 +236,30 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
 #pragma unroll
     for (int q = 0; q < Q; ++q) tacc[q] = P::zero();
     if (C == nullptr) {
-      gemm_accumulate<Q, MODE>(tacc, nq, m, n, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
+      gemm_accumulate<Q, MODE>(tacc, om, m, n, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
 #pragma unroll
-      for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, P::value(tacc[q]), acc[q]);
+      for (int q = 0; q < Q; ++q)
+        if (q < om.nv) acc[q] = fma(alpha, P::value(tacc[q]), acc[q]);
       continue;
     }
     // three-factor term: Ts = op(A)op(B) (m x nn), then acc += alpha * Ts op(C)
     const int nn = dimv(Tm.k2, x.slot);
-    if (nn > nb || m * nn > 256 * Q) {
+    if (nn <= 0) continue;
+    if (nn > nb || !fits(nn)) {
       if (threadIdx.x == 0) set_err(x, -9);
       return;
     }
-    const int nq2 = (m * nn + 255) / 256;
-    gemm_accumulate<Q, MODE>(tacc, nq2, m, nn, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
+    const OutMap om2 = out_map(m, nn);
+    gemm_accumulate<Q, MODE>(tacc, om2, m, nn, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      if (q < nq2 && e < m * nn) Ts[(e / nn) * ldbs + e % nn] = P::stage(P::value(tacc[q]));
-    }
+    for (int q = 0; q < Q; ++q)
+      if (q < om2.nv) Ts[(om2.r0 + q * om2.rstep) * ldbs + om2.c] = P::stage(P::value(tacc[q]));
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < Q; ++q) tacc[q] = P::zero();
     // Ts (m x nn) times op(C) (nn x n); Ts plays the role of A (already in smem)
+    const S* tr = Ts + om.r0 * ldbs;
+    const int tstep = om.rstep * ldbs;
     for (int kk = 0; kk < nn; kk += GK) {
       const int kc = min(GK, nn - kk);
       for (int e = threadIdx.x; e < kc * n; e += 256) {
@@ -234,32 +267,20 @@ __global__ void __launch_bounds__(256) k_gemm(const ExecCtx* __restrict__ px, co
         Bs[l * ldbs + c] = P::stage(ld_op(C, Tm.ldc, Tm.tc, kk + l, c));
       }
       __syncthreads();
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        if (q < nq) {
-          const int e = threadIdx.x + 256 * q;
-          if (e < m * n) {
-            const int r = e / n, c = e % n;
-            typename P::A a = tacc[q];
-            for (int l = 0; l < kc; ++l) P::fma_acc(a, Ts[r * ldbs + kk + l], Bs[l * ldbs + c]);
-            tacc[q] = a;
-          }
-        }
-      }
+      mac_rows<Q, MODE>(tacc, om.nv, tr + kk, tstep, Bs + om.c, ldbs, kc);
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = fma(alpha, P::value(tacc[q]), acc[q]);
+    for (int q = 0; q < Q; ++q)
+      if (q < om.nv) acc[q] = fma(alpha, P::value(tacc[q]), acc[q]);
   }
   double* out = ptrv(O.o, x);
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int e = threadIdx.x + 256 * q;
-    if (q < nq && e < m * n) {
-      double* p = out + (int64_t)(e / n) * O.ldo + e % n;
+  for (int q = 0; q < Q; ++q)
+    if (q < om.nv) {
+      double* p = out + (int64_t)(om.r0 + q * om.rstep) * O.ldo + om.c;
       *p = O.beta ? (*p + acc[q]) : acc[q];
     }
-  }
 }
 
 // ------------------------------------------------------------------ copy ----
@@ -1146,25 +1167,26 @@ void launch_finalize(const ExecCtx* x, int nrank, cudaStream_t s) {
   k_finalize<<<(nrank + 255) / 256 + 1, 256, 0, s>>>(x);
 }
 
+// qsteps = ceil(mmax / (256 / nb)): outputs per thread of the stage's largest tile
 template <int MODE>
-static void launch_gemm_mode(int cells, int count, size_t sm, cudaStream_t s, const ExecCtx* x, const GemmOut* go,
+static void launch_gemm_mode(int qsteps, int count, size_t sm, cudaStream_t s, const ExecCtx* x, const GemmOut* go,
                              const GemmTerm* gt, int mmax, int nb) {
-  if (cells <= 256)
+  if (qsteps <= 1)
     k_gemm<1, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
-  else if (cells <= 1024)
+  else if (qsteps <= 4)
     k_gemm<4, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
   else
     k_gemm<GQ, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
 }
 
-static void launch_gemm(int mode, int cells, int count, size_t sm, cudaStream_t s, const ExecCtx* x,
+static void launch_gemm(int mode, int qsteps, int count, size_t sm, cudaStream_t s, const ExecCtx* x,
                         const GemmOut* go, const GemmTerm* gt, int mmax, int nb) {
   if (mode == GM_DF)
-    launch_gemm_mode<GM_DF>(cells, count, sm, s, x, go, gt, mmax, nb);
+    launch_gemm_mode<GM_DF>(qsteps, count, sm, s, x, go, gt, mmax, nb);
   else if (mode == GM_F32)
-    launch_gemm_mode<GM_F32>(cells, count, sm, s, x, go, gt, mmax, nb);
+    launch_gemm_mode<GM_F32>(qsteps, count, sm, s, x, go, gt, mmax, nb);
   else
-    launch_gemm_mode<GM_F64>(cells, count, sm, s, x, go, gt, mmax, nb);
+    launch_gemm_mode<GM_F64>(qsteps, count, sm, s, x, go, gt, mmax, nb);
 }
 
 void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaStream_t s) {
@@ -1176,9 +1198,9 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaSt
       const int mmax = shape ? ((shape >> 16) & 0xff) : GT, nb = shape ? (shape & 0xffff) : GT;
       const int mode = (st.aux & GEMM_AUX_DF) ? GM_DF : (st.aux & GEMM_AUX_FP32) ? GM_F32 : GM_F64;
       const size_t sm = (mode == GM_F32 ? sizeof(float) : sizeof(double)) * gemm_smem_doubles(mmax, nb);
-      const int cells = mmax * nb;
+      const int rstep = 256 / nb;
       const GemmOut* go = j.gemm_out + st.first;
-      launch_gemm(mode, cells, st.count, sm, s, x, go, j.gemm_term, mmax, nb);
+      launch_gemm(mode, (mmax + rstep - 1) / rstep, st.count, sm, s, x, go, j.gemm_term, mmax, nb);
     }
       break;
     case ST_COPY:
