@@ -70,35 +70,101 @@ struct DF {
 template <int MODE>
 struct GemmPol;
 
+// Policy members: S staged operand, A inner (k-loop) accumulator, O outer
+// accumulator over the terms of an output; stage() converts a loaded
+// operand, restage() an inner result that becomes an operand again (the
+// middle product of a three-factor term), oadd(o, alpha, a) does
+// o += alpha * a, oadd_plain(o, alpha, v) does o += alpha * v, result()
+// returns the output value.
 template <>
 struct GemmPol<GM_F64> {
-  using S = double;  // staged operand
-  using A = double;  // inner accumulator
+  using S = double;
+  using A = double;
+  using O = double;
   __device__ static S stage(double v) { return v; }
+  __device__ static S restage(const A& a) { return a; }
   __device__ static A zero() { return 0.0; }
+  __device__ static O ozero() { return 0.0; }
   __device__ static void fma_acc(A& a, S x, S y) { a = fma(x, y, a); }
-  __device__ static double value(const A& a) { return a; }
+  __device__ static void oadd(O& o, double alpha, const A& a) { o = fma(alpha, a, o); }
+  __device__ static void oadd_plain(O& o, double alpha, double v) { o = fma(alpha, v, o); }
+  __device__ static double result(const O& o) { return o; }
 };
 
 template <>
 struct GemmPol<GM_F32> {
   using S = float;
   using A = float;
+  using O = double;
   __device__ static S stage(double v) { return (float)v; }
+  __device__ static S restage(const A& a) { return a; }
   __device__ static A zero() { return 0.0f; }
+  __device__ static O ozero() { return 0.0; }
   __device__ static void fma_acc(A& a, S x, S y) { a = fmaf(x, y, a); }
-  __device__ static double value(const A& a) { return (double)a; }
+  __device__ static void oadd(O& o, double alpha, const A& a) { o = fma(alpha, (double)a, o); }
+  __device__ static void oadd_plain(O& o, double alpha, double v) { o = fma(alpha, v, o); }
+  __device__ static double result(const O& o) { return o; }
 };
+
+// Split of an FP64 value into FP32 hi + lo without FP64 instructions (on this
+// GPU every FP64 instruction, conversions included, issues at 1/64 of the
+// FP32 rate).  hi = the value truncated to 24 significant bits (bit copy of
+// sign, re-biased exponent and the top 23 fraction bits); lo = the remaining
+// 29 fraction bits rounded to FP32 and scaled: |v - hi - lo| <= 2^-47 |v|.
+// Zero and values below FP32's normal range (|v| < 2^-126) give (0, 0);
+// |v| >= 2^128, inf and NaN take the plain conversion.
+__device__ __forceinline__ float2 split_df(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+  if (e < -126) return make_float2(0.0f, 0.0f);
+  if (e > 127) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  }
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned ebits = (unsigned)(e + 127) << 23;
+  const float hi = __uint_as_float(sign | ebits | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  const float rem = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), 0x1p-52f);  // < 2^-23
+  const float lo = __fmul_rn(rem, __uint_as_float(ebits));                    // rem * 2^e
+  return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
 
 template <>
 struct GemmPol<GM_DF> {
   using S = float2;  // (hi, lo)
   using A = DF;
-  __device__ static S stage(double v) {
-    const float hi = (float)v;
-    return make_float2(hi, (float)(v - (double)hi));
+  using O = DF;
+  __device__ static S stage(double v) { return split_df(v); }
+  // (s, c) renormalised by Fast2Sum (|c| <= |s| for these accumulators)
+  __device__ static S restage(const A& a) {
+    const float h = __fadd_rn(a.s, a.c);
+    return make_float2(h, __fsub_rn(a.c, __fsub_rn(h, a.s)));
   }
   __device__ static A zero() { return DF{0.0f, 0.0f}; }
+  __device__ static O ozero() { return DF{0.0f, 0.0f}; }
+  // o += (ph + pl) with ph = alpha_hi * a.s exact through an FMA: TwoSum on
+  // the leading parts, every error term into o.c
+  __device__ static void oadd(O& o, double alpha, const A& a) {
+    const float2 al = split_df(alpha);
+    const float ph = __fmul_rn(al.x, a.s);
+    float pl = fmaf(al.x, a.s, -ph);
+    pl = fmaf(al.x, a.c, pl);
+    pl = fmaf(al.y, a.s, pl);
+    add2(o, ph, pl);
+  }
+  __device__ static void oadd_plain(O& o, double alpha, double v) {
+    const float2 p = split_df(alpha * v);
+    add2(o, p.x, p.y);
+  }
+  __device__ static void add2(O& o, float h, float l) {
+    const float t = __fadd_rn(o.s, h);
+    const float z = __fsub_rn(t, o.s);
+    const float err = __fadd_rn(__fsub_rn(o.s, __fsub_rn(t, z)), __fsub_rn(h, z));
+    o.s = t;
+    o.c = __fadd_rn(__fadd_rn(o.c, err), l);
+  }
+  __device__ static double result(const O& o) { return (double)o.s + (double)o.c; }
   __device__ static void fma_acc(A& a, S x, S y) {
     const float p = __fmul_rn(x.x, y.x);
     const float e = fmaf(x.x, y.x, -p);  // x.hi * y.hi = p + e exactly
@@ -112,7 +178,6 @@ struct GemmPol<GM_DF> {
     c = fmaf(x.y, y.x, c);
     a.c = c;
   }
-  __device__ static double value(const A& a) { return (double)a.s + (double)a.c; }
 };
 
 // Outputs of this thread in an m x n tile: column c, rows r0 + q * rstep for
@@ -214,9 +279,9 @@ __global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const
     return;
   }
   const OutMap om = out_map(m, n);
-  double acc[Q];
+  typename P::O acc[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+  for (int q = 0; q < Q; ++q) acc[q] = P::ozero();
 
   for (int ti = O.t0; ti < O.t1; ++ti) {
     const GemmTerm& Tm = terms[ti];
@@ -228,7 +293,7 @@ __global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const
     if (B == nullptr) {  // plain add of op(A) (m x n)
 #pragma unroll
       for (int q = 0; q < Q; ++q)
-        if (q < om.nv) acc[q] = fma(alpha, ld_op(A, Tm.lda, Tm.ta, om.r0 + q * om.rstep, om.c), acc[q]);
+        if (q < om.nv) P::oadd_plain(acc[q], alpha, ld_op(A, Tm.lda, Tm.ta, om.r0 + q * om.rstep, om.c));
       continue;
     }
     const int k1 = dimv(Tm.k1, x.slot);
@@ -239,7 +304,7 @@ __global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const
       gemm_accumulate<Q, MODE>(tacc, om, m, n, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
 #pragma unroll
       for (int q = 0; q < Q; ++q)
-        if (q < om.nv) acc[q] = fma(alpha, P::value(tacc[q]), acc[q]);
+        if (q < om.nv) P::oadd(acc[q], alpha, tacc[q]);
       continue;
     }
     // three-factor term: Ts = op(A)op(B) (m x nn), then acc += alpha * Ts op(C)
@@ -253,7 +318,7 @@ __global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const
     gemm_accumulate<Q, MODE>(tacc, om2, m, nn, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
-      if (q < om2.nv) Ts[(om2.r0 + q * om2.rstep) * ldbs + om2.c] = P::stage(P::value(tacc[q]));
+      if (q < om2.nv) Ts[(om2.r0 + q * om2.rstep) * ldbs + om2.c] = P::restage(tacc[q]);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < Q; ++q) tacc[q] = P::zero();
@@ -272,14 +337,15 @@ __global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q)
-      if (q < om.nv) acc[q] = fma(alpha, P::value(tacc[q]), acc[q]);
+      if (q < om.nv) P::oadd(acc[q], alpha, tacc[q]);
   }
   double* out = ptrv(O.o, x);
 #pragma unroll
   for (int q = 0; q < Q; ++q)
     if (q < om.nv) {
       double* p = out + (int64_t)(om.r0 + q * om.rstep) * O.ldo + om.c;
-      *p = O.beta ? (*p + acc[q]) : acc[q];
+      const double v = P::result(acc[q]);
+      *p = O.beta ? (*p + v) : v;
     }
 }
 
