@@ -290,7 +290,7 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
     CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
     const int kind = i < ns ? (P.stages[i].kind == ST_NORM ? 7 : P.stages[i].kind) : 6;
     h2_kernel_prof& pr = prof[kind];
-    pr.launches += 1;
+    pr.launches += i < ns ? stage_launches(P.stages[i]) : 1;
     pr.ms += ms;
     if (i == ns) continue;
     const Stage& st = P.stages[i];
@@ -834,7 +834,8 @@ static int enqueue_product(const MulArgs& m, PlanRT& rt, cudaStream_t s, h2_kern
   C->off_WF = C->off_VF + (int64_t)(C->rows->depth + 1) * C->rows->n * P.kpad;
   C->arena_len = C->off_WF + (int64_t)(C->cols->depth + 1) * C->cols->n * P.kpad;
   C->nagglomerated = P.nagg;
-  C->launches = (int)P.stages.size() + 1;
+  C->launches = 1;  // the finalize kernel
+  for (const Stage& st : P.stages) C->launches += stage_launches(st);
   C->workspace_bytes = (P.ws_len + P.fac_len) * 8;
   C->uid = ++g_uid;
   C->stream = s;

@@ -8,6 +8,7 @@
 //   k_scan    prefix sums of adaptive ranks (panel column offsets)
 // One CTA processes one job; FP64 arithmetic throughout.
 #include <cuda_runtime.h>
+#include <climits>
 #include <math.h>
 #include <stdint.h>
 
@@ -808,8 +809,12 @@ __device__ __forceinline__ int svd_pair_j(int rnd, int p, int ce) {
   return max(svd_pair_a(rnd, p, ce), svd_pair_b(rnd, p, ce));
 }
 
+// A launch may take only the jobs whose shared-memory need (per-column
+// arrays and matrix, in doubles; 0 for an empty job) lies in
+// (need_lo, need_hi]: a stage of mixed sizes then runs its small jobs in
+// small CTAs, many per SM, and its large ones in a second launch.
 __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, const SvdJob* __restrict__ jobs,
-                                             int64_t first, int smem_doubles, int cmax) {
+                                                int64_t first, int smem_doubles, int cmax, int need_lo, int need_hi) {
   const ExecCtx& x = *px;
   extern __shared__ double sdyn[];
   __shared__ int rotated;
@@ -819,6 +824,10 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
   __shared__ double s_fro;
   const SvdJob& J = jobs[blockIdx.x];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
+  {
+    const int64_t need = (rows <= 0 || cols <= 0) ? 0 : svd_colarr_doubles(cols) + (int64_t)(rows + 1) * cols;
+    if (need <= need_lo || need > need_hi) return;  // the other launch of the stage
+  }
   // per-column arrays sized for this job's columns, the matrix behind them
   const int ca = svd_colarr_doubles(cols);
   double* nrm2 = sdyn;                 // squared column norms
@@ -1255,6 +1264,10 @@ static void launch_gemm(int mode, int qsteps, int count, size_t sm, cudaStream_t
     launch_gemm_mode<GM_F64>(qsteps, count, sm, s, x, go, gt, mmax, nb);
 }
 
+int stage_launches(const Stage& st) {
+  return (st.kind == ST_SVD && st.smem > 8 * SVD_SMALL_DOUBLES) ? 2 : 1;
+}
+
 void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaStream_t s) {
   if (st.count <= 0) return;
   switch (st.kind) {
@@ -1284,7 +1297,16 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaSt
       // per-column arrays of any job and the matrices that fit
       const int cmax = st.aux > 0 ? st.aux : SVD_MAXDIM;
       const size_t sm = st.smem > 0 ? (size_t)st.smem : 8 * (size_t)SVD_SMEM_DOUBLES;
-      k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first, (int)(sm / 8), cmax);
+      if (stage_launches(st) == 2) {
+        // jobs that fit SVD_SMALL_DOUBLES in 128-thread CTAs (five per SM),
+        // the rest in the stage's full-size CTAs
+        k_svd<<<st.count, 128, 8 * (size_t)SVD_SMALL_DOUBLES, s>>>(x, j.svd + st.first, st.first, SVD_SMALL_DOUBLES,
+                                                                   cmax, -1, SVD_SMALL_DOUBLES);
+        k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first, (int)(sm / 8), cmax, SVD_SMALL_DOUBLES,
+                                        INT_MAX);
+      } else {
+        k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first, (int)(sm / 8), cmax, -1, INT_MAX);
+      }
     }
       break;
     case ST_NORM:

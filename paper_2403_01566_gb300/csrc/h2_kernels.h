@@ -15,6 +15,9 @@ constexpr int GEMM_AUX_DF = 1 << 25;    // Stage::aux flag of a GEMM stage: comp
 // leaves ~90 KB of L1 to the matrices that stay in global memory; a 72 KB cap
 // (three CTAs, ~26 KB of L1) ran those 2.3x slower.
 constexpr int SVD_SMEM_DOUBLES = 9732;
+// SVD jobs needing at most this much shared memory (doubles, 40 KB) run in
+// 128-thread CTAs, five per SM, when their stage also holds larger jobs
+constexpr int SVD_SMALL_DOUBLES = 5120;
 
 #ifdef __CUDACC__
 #define H2_HOST_DEVICE __host__ __device__
@@ -44,6 +47,8 @@ struct DeviceJobs {
 
 cudaError_t kernels_init();
 size_t gemm_smem_bytes();
+// kernel launches of a stage (an SVD stage of mixed job sizes takes two)
+int stage_launches(const Stage& st);
 void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaStream_t s);
 void launch_finalize(const ExecCtx* x, int nrank, cudaStream_t s);
 
