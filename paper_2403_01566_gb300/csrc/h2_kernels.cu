@@ -166,6 +166,8 @@ struct GemmPol<GM_DF> {
     o.c = __fadd_rn(__fadd_rn(o.c, err), l);
   }
   __device__ static double result(const O& o) { return (double)o.s + (double)o.c; }
+  // The error terms of one step are summed first, so that each of a.s and
+  // a.c carries a single dependent add from one k step to the next.
   __device__ static void fma_acc(A& a, S x, S y) {
     const float p = __fmul_rn(x.x, y.x);
     const float e = fmaf(x.x, y.x, -p);  // x.hi * y.hi = p + e exactly
@@ -173,11 +175,9 @@ struct GemmPol<GM_DF> {
     const float z = __fsub_rn(t, a.s);
     const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(p, z));
     a.s = t;
-    float c = __fadd_rn(a.c, err);
-    c = __fadd_rn(c, e);
-    c = fmaf(x.x, y.y, c);
-    c = fmaf(x.y, y.x, c);
-    a.c = c;
+    float u = fmaf(x.x, y.y, e);
+    u = fmaf(x.y, y.x, u);
+    a.c = __fadd_rn(a.c, __fadd_rn(u, err));
   }
 };
 
@@ -199,25 +199,42 @@ __device__ __forceinline__ OutMap out_map(int m, int n) {
   return o;
 }
 
-// acc[q] += sum_l a[q * astep + l] b[l * ldb] (l < kc) for q < nv.  FP64
-// issue is the bound in the FP64 mode, so one output at a time; the FP32 and
-// compensated modes run four independent chains per pass to cover the latency
-// of their dependent FP32 steps.
+// acc[q] += sum_l a[q * astep + l] b[l * ldb] (l < kc) for q < nv, one
+// output at a time (interleaving 2, 4 or 8 outputs measured slower in every
+// mode).
 template <int Q, int MODE>
 __device__ __forceinline__ void mac_rows(typename GemmPol<MODE>::A (&acc)[Q], int nv,
                                          const typename GemmPol<MODE>::S* a, int astep,
                                          const typename GemmPol<MODE>::S* b, int ldb, int kc) {
   using P = GemmPol<MODE>;
-  constexpr int CH = MODE == GM_F64 ? 1 : 4;
 #pragma unroll
-  for (int q0 = 0; q0 < Q; q0 += CH)
-    if (q0 < nv)
-      for (int l = 0; l < kc; ++l) {
-        const typename P::S bv = b[l * ldb];
-#pragma unroll
-        for (int u = 0; u < CH; ++u)
-          if (q0 + u < Q && q0 + u < nv) P::fma_acc(acc[q0 + u], a[(q0 + u) * astep + l], bv);
-      }
+  for (int q = 0; q < Q; ++q)
+    if (q < nv) {
+      typename P::A t = acc[q];
+      for (int l = 0; l < kc; ++l) P::fma_acc(t, a[q * astep + l], b[l * ldb]);
+      acc[q] = t;
+    }
+}
+
+// dst[i * ldd + j] = stage(op(src)(i0 + i, j0 + j)) for i < R, j < Cc, with
+// op(src)(i, j) = src[j * ld + i] if t else src[i * ld + j].  All threads
+// share the R x Cc elements; consecutive threads take consecutive source
+// addresses in both orientations.
+template <int MODE>
+__device__ __forceinline__ void stage_tile(typename GemmPol<MODE>::S* dst, int ldd, const double* src, int ld,
+                                           int t, int R, int Cc, int i0, int j0) {
+  using P = GemmPol<MODE>;
+  if (!t) {
+    for (int e = threadIdx.x; e < R * Cc; e += blockDim.x) {
+      const int i = e / Cc, j = e % Cc;
+      dst[i * ldd + j] = P::stage(src[(int64_t)(i0 + i) * ld + j0 + j]);
+    }
+  } else {
+    for (int e = threadIdx.x; e < R * Cc; e += blockDim.x) {
+      const int j = e / R, i = e % R;
+      dst[i * ldd + j] = P::stage(src[(int64_t)(j0 + j) * ld + i0 + i]);
+    }
+  }
 }
 
 // acc[q] += op(A)(m x k) op(B)(k x n) for the outputs of this thread
@@ -232,14 +249,8 @@ __device__ __forceinline__ void gemm_accumulate(typename GemmPol<MODE>::A (&acc)
   const int astep = om.rstep * (GK + 1);
   for (int kk = 0; kk < k; kk += GK) {
     const int kc = min(GK, k - kk);
-    for (int e = threadIdx.x; e < m * kc; e += 256) {
-      const int r = e / kc, l = e % kc;
-      As[r * (GK + 1) + l] = P::stage(ld_op(A, lda, ta, r, kk + l));
-    }
-    for (int e = threadIdx.x; e < kc * n; e += 256) {
-      const int l = e / n, c = e % n;
-      Bs[l * ldbs + c] = P::stage(ld_op(B, ldb, tb, kk + l, c));
-    }
+    stage_tile<MODE>(As, GK + 1, A, lda, ta, m, kc, 0, kk);
+    stage_tile<MODE>(Bs, ldbs, B, ldb, tb, kc, n, kk, 0);
     __syncthreads();
     mac_rows<Q, MODE>(acc, om.nv, ar, astep, Bs + om.c, ldbs, kc);
     __syncthreads();
@@ -328,10 +339,7 @@ __global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const
     const int tstep = om.rstep * ldbs;
     for (int kk = 0; kk < nn; kk += GK) {
       const int kc = min(GK, nn - kk);
-      for (int e = threadIdx.x; e < kc * n; e += 256) {
-        const int l = e / n, c = e % n;
-        Bs[l * ldbs + c] = P::stage(ld_op(C, Tm.ldc, Tm.tc, kk + l, c));
-      }
+      stage_tile<MODE>(Bs, ldbs, C, Tm.ldc, Tm.tc, kc, n, kk, 0);
       __syncthreads();
       mac_rows<Q, MODE>(tacc, om.nv, tr + kk, tstep, Bs + om.c, ldbs, kc);
       __syncthreads();
