@@ -418,6 +418,75 @@ __device__ __forceinline__ void householder_scalars(double alpha, double s2, dou
 
 constexpr int QR_MAXPIV = 256;  // largest column count of a pivoted QR
 
+// Unpivoted Householder QR of a column-major matrix (rows x cols, leading
+// dimension lda, global or shared memory) with one step of look-ahead: while
+// warps 1.. apply reflector j to columns j+2.., warp 0 applies it to column
+// j+1 and forms reflector j+1 from the result, so a step needs one block
+// barrier and the reflector's serial work overlaps the trailing update.
+// Reflector scalars alternate between sh[0] and sh[1].  Returns min(rows, cols).
+__device__ int householder_cols_la(double* a, int lda, int rows, int cols, double* tau, double* sh) {
+  const int q = min(rows, cols);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (q <= 0) return 0;
+  // warp 0: reflector of column j from its current contents
+  auto form = [&](int j) {
+    double* col = a + (int64_t)j * lda;
+    const double alpha = col[j];
+    double s2 = 0.0;
+    for (int i = j + 1 + lane; i < rows; i += 32) s2 = fma(col[i], col[i], s2);
+    s2 = warp_sum(s2);
+    double t = 0.0;
+    if (s2 > 0.0) {
+      double beta, sc;
+      householder_scalars(alpha, s2, beta, t, sc);
+      for (int i = j + 1 + lane; i < rows; i += 32) col[i] *= sc;
+      __syncwarp();
+      if (lane == 0) col[j] = beta;
+    }
+    if (lane == 0) {
+      sh[j & 1] = t;
+      if (tau) tau[j] = t;
+    }
+    __syncwarp();
+  };
+  // column c -= t v (v^T c), v = [1; col_j below j], by a team of ts lanes of one warp
+  auto apply = [&](int j, double t, int c, int tl, int ts) {
+    const double* vj = a + (int64_t)j * lda;
+    double p = 0.0, cj = 0.0;
+    double* cc = a + (int64_t)c * lda;
+    if (c < cols) {
+      cj = cc[j];
+      for (int i = j + 1 + tl; i < rows; i += ts) p = fma(vj[i], cc[i], p);
+    }
+    for (int o = ts >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    const double w = t * (cj + p);
+    if (c < cols) {
+      if (tl == 0) cc[j] -= w;
+      for (int i = j + 1 + tl; i < rows; i += ts) cc[i] = fma(-w, vj[i], cc[i]);
+    }
+  };
+  if (warp == 0) form(0);
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    const double t = sh[j & 1];
+    if (warp == 0) {
+      if (j + 1 < cols) {
+        if (t != 0.0) apply(j, t, j + 1, lane, 32);
+        __syncwarp();
+        if (j + 1 < q) form(j + 1);
+      }
+    } else if (t != 0.0) {
+      const int len = rows - j - 1;
+      int ts = 32;
+      while (ts > 1 && ts * 8 > len) ts >>= 1;
+      const int tid = threadIdx.x - 32, nteam = ((int)blockDim.x - 32) / ts, team = tid / ts, tl = tid % ts;
+      for (int c0 = j + 2; c0 < cols; c0 += nteam) apply(j, t, c0 + team, tl, ts);
+    }
+    __syncthreads();
+  }
+  return q;
+}
+
 // Householder QR on a column-major matrix a (rows x cols, leading dimension
 // lda), in place; `a` is global or shared memory.  With piv != nullptr the
 // columns are pivoted (column of largest remaining norm first, lowest index on
@@ -427,13 +496,15 @@ constexpr int QR_MAXPIV = 256;  // largest column count of a pivoted QR
 //
 // Each step: warp 0 alone picks the pivot, swaps, forms the reflector and
 // scales it (no block barrier inside), then all warps update the trailing
-// columns; two block barriers per step.
+// columns; two block barriers per step.  Without pivoting the look-ahead
+// variant above runs instead.
 //
 // With pivoting and floor2 > 0 the factorisation stops at the first step j
 // whose trailing columns hold a squared Frobenius norm (the sum of cn) <=
 // floor2 * ||a||_F^2; tau[j..] is then 0.  Returns the number of steps taken.
 __device__ int householder_cols(double* a, int lda, int rows, int cols, double* tau, double* sh, int* piv,
                                 double* cn, double* cn0, double floor2 = -1.0) {
+  if (!piv) return householder_cols_la(a, lda, rows, cols, tau, sh);
   const int q = min(rows, cols);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   constexpr double kRecompute = 1.4901161193847656e-08;  // 2^-26
@@ -730,21 +801,29 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
   if (rank_out && threadIdx.x == 0) *rank_out = rk;
 }
 
-// out = H_0 ... H_{q-1} [Y; 0].  Threads: column c = tid % nc of out, row
-// segment tid / nc (rows strided by the segment count); per reflector the
-// partial dot products meet in shared memory and one thread per column sums
-// them, so no FP64 shuffle reductions are issued.
+// out = H_0 ... H_{q-1} [Y; 0], the reflectors applied QB at a time (last
+// block first).  For a block H_{j0} ... H_{j1-1} and each column o of out:
+//   d_k = v_k^T o (all k of the block, one pass over o),
+//   w_k = tau_k (d_k - sum_{m > k} (v_k^T v_m) w_m)   (k = j1-1 down to j0),
+//   o  -= sum_k v_k w_k                                (one more pass),
+// which equals applying H_{j1-1} first and H_{j0} last.  Threads: column
+// c = tid % nc of out, row segment tid / nc; the partial dots meet in shared
+// memory and one thread per column sums them (no FP64 shuffle reductions on
+// the columns); the block's reflector products v_k^T v_m are one warp each.
+// A block reads and writes out once and takes three barriers, not QB times.
+constexpr int QB = 4;
 __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, const QApplyJob* __restrict__ jobs) {
   const ExecCtx& x = *px;
-  __shared__ double part[256];
-  __shared__ double wsh[256];
+  __shared__ double part[QB][256];
+  __shared__ double wsh[QB][256];
+  __shared__ double gsh[QB * QB];
   const QApplyJob& J = jobs[blockIdx.x];
   const int rows = dimv(J.rows, x.slot), q = dimv(J.q, x.slot), nc = dimv(J.ncols, x.slot);
   const double* a = ptrv(J.a, x);
   const double* tau = ptrv(J.tau, x);
   const double* y = ptrv(J.y, x);
   double* out = ptrv(J.out, x);
-  const int ldo = J.ldo;
+  const int ldo = J.ldo, lda = J.lda;
   if (nc > (int)blockDim.x) {
     if (threadIdx.x == 0) set_err(x, -9);
     return;
@@ -758,26 +837,57 @@ __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, 
   const int nseg = blockDim.x / nc;
   const int c = threadIdx.x % nc, sg = threadIdx.x / nc;
   const bool active = sg < nseg;
-  for (int j = min(q, rows) - 1; j >= 0; --j) {
-    const double t = tau[j];
-    if (t == 0.0) continue;
-    const double* v = a + (int64_t)j * J.lda;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  // v_k[i]: 1 at i = k, the stored reflector below, 0 above
+  auto vk = [&](int k, int i) { return i > k ? a[(int64_t)k * lda + i] : (i == k ? 1.0 : 0.0); };
+  for (int j1 = min(q, rows); j1 > 0; j1 -= QB) {
+    const int j0 = max(0, j1 - QB), nb = j1 - j0;
+    // v_u^T v_m for u < m of the block, one warp each
+    for (int pr = warp; pr < QB * QB; pr += nwarp) {
+      const int u = pr / QB, m = pr % QB;
+      if (u < m && m < nb) {
+        const int ku = j0 + u, km = j0 + m;
+        double sdot = 0.0;
+        for (int i = km + 1 + lane; i < rows; i += 32)
+          sdot = fma(a[(int64_t)ku * lda + i], a[(int64_t)km * lda + i], sdot);
+        sdot = warp_sum(sdot);
+        if (lane == 0) gsh[u * QB + m] = a[(int64_t)ku * lda + km] + sdot;
+      }
+    }
     if (active) {
-      double p = sg == 0 ? out[(int64_t)j * ldo + c] : 0.0;
-      for (int i = j + 1 + sg; i < rows; i += nseg) p = fma(v[i], out[(int64_t)i * ldo + c], p);
-      part[sg * nc + c] = p;
+      double d[QB];
+#pragma unroll
+      for (int u = 0; u < QB; ++u) d[u] = 0.0;
+      for (int i = j0 + sg; i < rows; i += nseg) {
+        const double o = out[(int64_t)i * ldo + c];
+#pragma unroll
+        for (int u = 0; u < QB; ++u)
+          if (u < nb) d[u] = fma(vk(j0 + u, i), o, d[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < QB; ++u) part[u][sg * nc + c] = d[u];
     }
     __syncthreads();
     if ((int)threadIdx.x < nc) {
-      double sum = part[threadIdx.x];
-      for (int g = 1; g < nseg; ++g) sum += part[g * nc + threadIdx.x];
-      wsh[threadIdx.x] = t * sum;
+      for (int u = nb - 1; u >= 0; --u) {
+        double sum = part[u][threadIdx.x];
+        for (int g = 1; g < nseg; ++g) sum += part[u][g * nc + threadIdx.x];
+        for (int m = u + 1; m < nb; ++m) sum -= gsh[u * QB + m] * wsh[m][threadIdx.x];
+        wsh[u][threadIdx.x] = tau[j0 + u] * sum;
+      }
     }
     __syncthreads();
     if (active) {
-      const double w = wsh[c];
-      if (sg == 0) out[(int64_t)j * ldo + c] -= w;
-      for (int i = j + 1 + sg; i < rows; i += nseg) out[(int64_t)i * ldo + c] = fma(-w, v[i], out[(int64_t)i * ldo + c]);
+      double w[QB];
+#pragma unroll
+      for (int u = 0; u < QB; ++u) w[u] = u < nb ? wsh[u][c] : 0.0;
+      for (int i = j0 + sg; i < rows; i += nseg) {
+        double o = out[(int64_t)i * ldo + c];
+#pragma unroll
+        for (int u = 0; u < QB; ++u)
+          if (u < nb) o = fma(-vk(j0 + u, i), w[u], o);
+        out[(int64_t)i * ldo + c] = o;
+      }
     }
     __syncthreads();
   }
