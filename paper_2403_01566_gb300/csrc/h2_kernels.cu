@@ -673,44 +673,58 @@ __device__ void tsqr_r(const double* __restrict__ a, int lda, int rows, int cols
       C[c * ld + i] = a[(int64_t)c * lda + r0 + i];
     }
     __syncthreads();
+    // one step of look-ahead, as in householder_cols_la: while warps 1..
+    // apply reflector j to columns j+2.., warp 0 applies it to column j+1 and
+    // forms reflector j+1; the scalars alternate between sh[0] and sh[1]
+    auto form = [&](int j) {  // warp 0: reflector of [W(j, j); C(:, j)]
+      double* cj = C + j * ld;
+      double s2 = 0.0;
+      for (int i = lane; i < ch; i += 32) s2 = fma(cj[i], cj[i], s2);
+      s2 = warp_sum(s2);
+      const double alpha = W[j * ld + j];
+      double t = 0.0;
+      if (s2 > 0.0) {
+        double beta, sc;
+        householder_scalars(alpha, s2, beta, t, sc);
+        for (int i = lane; i < ch; i += 32) cj[i] *= sc;
+        __syncwarp();
+        if (lane == 0) W[j * ld + j] = beta;
+      }
+      if (lane == 0) sh[j & 1] = t;
+      __syncwarp();
+    };
+    // [W(j, c); C(:, c)] -= t v (v^T [W(j, c); C(:, c)]), v = [1; C(:, j)], by a
+    // team of ts lanes of one warp
+    auto apply = [&](int j, double t, int c, int tl, int ts) {
+      const double* cj = C + j * ld;
+      double p = 0.0, rjc = 0.0;
+      double* cc = C + c * ld;
+      if (c < cols) {
+        rjc = W[c * ld + j];  // read by every lane before the shuffle (lane 0 writes it below)
+        for (int i = tl; i < ch; i += ts) p = fma(cj[i], cc[i], p);
+      }
+      for (int o = ts >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+      if (c < cols) {
+        const double w = t * (rjc + p);
+        if (tl == 0) W[c * ld + j] = rjc - w;
+        for (int i = tl; i < ch; i += ts) cc[i] = fma(-w, cj[i], cc[i]);
+      }
+    };
     int ts = 32;
     while (ts > 1 && ts * 8 > ch) ts >>= 1;
-    const int nteam = blockDim.x / ts, team = threadIdx.x / ts, tl = threadIdx.x % ts;
+    const int tid = threadIdx.x - 32, nteam = ((int)blockDim.x - 32) / ts, team = tid / ts, tl = tid % ts;
+    if (warp == 0) form(0);
+    __syncthreads();
     for (int j = 0; j < cols; ++j) {
-      double* cj = C + j * ld;
+      const double t = sh[j & 1];
       if (warp == 0) {
-        double s2 = 0.0;
-        for (int i = lane; i < ch; i += 32) s2 = fma(cj[i], cj[i], s2);
-        s2 = warp_sum(s2);
-        const double alpha = W[j * ld + j];
-        double t = 0.0;
-        if (s2 > 0.0) {
-          double beta, sc;
-          householder_scalars(alpha, s2, beta, t, sc);
-          for (int i = lane; i < ch; i += 32) cj[i] *= sc;
+        if (j + 1 < cols) {
+          if (t != 0.0) apply(j, t, j + 1, lane, 32);
           __syncwarp();
-          if (lane == 0) W[j * ld + j] = beta;
+          form(j + 1);
         }
-        if (lane == 0) sh[0] = t;
-      }
-      __syncthreads();
-      const double t = sh[0];
-      if (t != 0.0) {
-        for (int c0 = j + 1; c0 < cols; c0 += nteam) {
-          const int c = c0 + team;
-          double p = 0.0, rjc = 0.0;
-          double* cc = C + c * ld;
-          if (c < cols) {
-            rjc = W[c * ld + j];  // read by every lane before the shuffle (lane 0 writes it below)
-            for (int i = tl; i < ch; i += ts) p = fma(cj[i], cc[i], p);
-          }
-          for (int o = ts >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-          if (c < cols) {
-            const double w = t * (rjc + p);
-            if (tl == 0) W[c * ld + j] = rjc - w;
-            for (int i = tl; i < ch; i += ts) cc[i] = fma(-w, cj[i], cc[i]);
-          }
-        }
+      } else if (t != 0.0) {
+        for (int c0 = j + 2; c0 < cols; c0 += nteam) apply(j, t, c0 + team, tl, ts);
       }
       __syncthreads();
     }
