@@ -732,7 +732,7 @@ __device__ void tsqr_r(const double* __restrict__ a, int lda, int rows, int cols
 }
 
 constexpr int QR_TSQR_MAXC = 64;       // widest R-only factorisation that streams row chunks
-constexpr int QR_MAX_SMEM_BYTES = 8 * (QR_TSQR_MAXC + 64) * QR_TSQR_MAXC;  // 64 KB
+constexpr int QR_MAX_SMEM_BYTES = 8 * (QR_TSQR_MAXC + 128) * QR_TSQR_MAXC;  // 96 KB
 
 // R output of a QR job (see QrJob::rmode): R(i, c) = src[c * lds + i] above
 // the diagonal for i < q, zero elsewhere.  Call after a block barrier (the

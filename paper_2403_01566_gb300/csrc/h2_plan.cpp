@@ -203,11 +203,16 @@ struct Builder {
     if (need <= cap) {
       qr_smem = (int)std::max<int64_t>(qr_smem, need * 8);
     } else if (!keep && maxc <= 64) {
-      // R-only: may stream 64-row chunks under the triangle
+      // R-only: may stream row chunks under the triangle, 128 rows for
+      // panels taller than 512 rows, else 64
       qr_tsqr = (int)std::max<int64_t>(qr_tsqr, (int64_t)(maxc + 64) * maxc * 8);
+      qr_tsqr_big = (int)std::max<int64_t>(qr_tsqr_big, (int64_t)(maxc + 128) * maxc * 8);
+      ++qr_stream_jobs;
+      if (maxr > 512) ++qr_stream_tall;
+      if (trunc_idx >= 0) ++qr_stream_trunc;
     }
   }
-  int qr_tsqr = 0;
+  int qr_tsqr = 0, qr_tsqr_big = 0, qr_stream_jobs = 0, qr_stream_tall = 0, qr_stream_trunc = 0;
   // Jobs of one stage are independent: issue them largest first so that the
   // long ones do not start last and leave the tail of the launch to a few SMs.
   template <class Job>
@@ -225,16 +230,25 @@ struct Builder {
     if (qj.empty()) return;
     largest_first(qj, qj_cost);
     qj_cost.clear();
-    // Streaming row chunks trades L2 traffic for more, shorter steps: a win
-    // when many jobs keep every SM busy, a loss for a few latency-bound ones,
-    // which then run in global memory.
+    // Streaming row chunks trades L2 traffic for more, shorter steps.  The
+    // 96 KB launch (128-row chunks, and jobs of up to 12288 elements wholly in
+    // shared memory) wins for stages of mostly tall panels (over 512 rows) and
+    // for QRs that stop at the noise floor (in shared memory they stop early;
+    // streamed, every column is reduced before the truncated pivoted QR of the
+    // triangle).  64-row chunks (three CTAs per SM) win when many short jobs
+    // keep every SM busy; a few latency-bound short ones run faster in global
+    // memory.  (grid2d n=16384: the 512 basis panels of ~915 rows 8.4 -> 7.7
+    // ms, the condensed merge QRs 5.2 -> 4.4 ms; the 96 KB launch for a stage
+    // of mostly short panels 2.5 -> 2.9 ms.)
     int smem = qr_smem;
-    if (qj.size() >= 2048) smem = std::max(smem, qr_tsqr);
+    if (qr_stream_tall > 0 && 2 * qr_stream_tall >= qr_stream_jobs) smem = std::max(smem, qr_tsqr_big);
+    else if (qr_stream_trunc > 0) smem = std::max(smem, qr_tsqr_big);
+    else if (qj.size() >= 2048) smem = std::max(smem, qr_tsqr);
     P.stages.push_back(Stage{ST_QR, (int64_t)P.qr.size(), (int)qj.size(), tag, smem});
     P.qr.insert(P.qr.end(), qj.begin(), qj.end());
     qj.clear();
     qr_smem = 0;
-    qr_tsqr = 0;
+    qr_tsqr = qr_tsqr_big = qr_stream_jobs = qr_stream_tall = qr_stream_trunc = 0;
   }
   void qapply(Ptr a, int lda, Ptr tau, Dim rows, Dim q, Ptr y, int ldy, Dim ncols, Ptr outp, int ldo) {
     qa.push_back(QApplyJob{a, tau, y, outp, lda, ldy, ldo, rows, q, ncols});
