@@ -1084,8 +1084,18 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
           const double ga = gt * di * dj, al = nrm2[i], be = nrm2[j];
           // |ga| > tol * sqrt(al * be), in squared form
           if (ga != 0.0 && al > tiny2 && be > tiny2 && ga * ga > (tol * tol) * al * be) {
-            const double zeta = (be - al) / (2.0 * ga);
-            const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            // t = tan(theta), the smaller root of t^2 + 2 zeta t - 1 = 0 with
+            // zeta = d / g2 (d = be - al, g2 = 2 ga), written as
+            // t = sign(d) g2 / (|d| + sqrt(d^2 + g2^2)) with d and g2 first
+            // scaled by a power of two into [1, 2) (no overflow): one
+            // reciprocal square root and one division on the round's
+            // critical path instead of two divisions and a square root
+            const double d0 = be - al, g0 = 2.0 * ga;
+            const double mx = fmax(fabs(d0), fabs(g0));
+            const double p2 = __hiloint2double((2046 - ((__double2hiint(mx) >> 20) & 0x7ff)) << 20, 0);
+            const double dd = d0 * p2, gg = g0 * p2;
+            const double n2 = fma(dd, dd, gg * gg);
+            const double t = copysign(1.0, d0) * gg / fma(n2, rsqrt(n2), fabs(dd));
             const double q = 1.0 + t * t;
             const double c = rsqrt(q);
             const double ei = dinv[i], ej = dinv[j];
