@@ -203,8 +203,8 @@ struct Builder {
     if (need <= cap) {
       qr_smem = (int)std::max<int64_t>(qr_smem, need * 8);
     } else if (!keep && maxc <= 64) {
-      // R-only: may stream row chunks under the triangle, 128 rows for
-      // panels taller than 512 rows, else 64
+      // R-only: may stream row chunks under the triangle (64 or 128 rows,
+      // chosen per stage in flush_qr)
       qr_tsqr = (int)std::max<int64_t>(qr_tsqr, (int64_t)(maxc + 64) * maxc * 8);
       qr_tsqr_big = (int)std::max<int64_t>(qr_tsqr_big, (int64_t)(maxc + 128) * maxc * 8);
       ++qr_stream_jobs;
@@ -268,11 +268,11 @@ struct Builder {
     P.svd_maxrows = std::max(P.svd_maxrows, rows);
     P.svd_maxcols = std::max(P.svd_maxcols, cols);
   }
-  // One launch per stage: shared memory for the largest job (its per-column
-  // arrays and matrix), capped at SVD_SMEM_DOUBLES; the matrices of larger
-  // jobs run in place in global memory.  (A separate
-  // one-CTA-per-SM launch for the large jobs measured no faster: it
-  // serialises behind the small ones.)
+  // One stage: shared memory for its largest job (per-column arrays and
+  // matrix), capped at SVD_SMEM_DOUBLES; the matrices of larger jobs run in
+  // place in global memory, and the launch code runs the small jobs of a
+  // mixed stage in small CTAs of their own.  (A one-CTA-per-SM launch for
+  // the large jobs measured no faster: it serialises behind the small ones.)
   void flush_svd(int tag) {
     if (sv.empty()) return;
     const int smem = (int)(sizeof(double) * std::max<int64_t>(svd_colarr_doubles(sv_maxc),
@@ -1055,7 +1055,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       const int64_t mark = B.ws;
       struct Scr {
         int64_t W1, W2, tau1, tau2, rho1, rho2, Gc, Wc, tauc, rhoc, U, sig, piv;
-        bool two_step;            // SVD through a second QR (M too tall for shared memory)
+        bool two_step;            // SVD through a second QR (M may not fit the SVD's shared memory)
         int64_t tau2c, R2, Y;     // its reflector scalars, triangle and small singular vectors
         int rslot;                // rows of rho_c kept above the noise floor (slot)
         int qc_max;
