@@ -1,12 +1,17 @@
 // Batched FP64 kernels for sm_103a that execute the stage lists built by the
 // planner (see h2_ops.h):
-//   k_gemm    grouped small GEMM chains with index gathers (out = sum A B [C])
+//   k_gemm    grouped small GEMM chains with index gathers (out = sum A B [C]),
+//             in FP64, FP32 or compensated FP32 (the precision forms)
 //   k_copy    strided copies / transposes / scalings with zero padding
-//   k_qr      Householder QR (the thin QR factorizations of Sections 5.1-5.2)
+//   k_qr      Householder QR (the thin QR factorizations of Sections 5.1-5.2),
+//             column-pivoted where an SVD follows, optionally stopped at a
+//             noise floor
 //   k_qapply  application of the thin Q factor to a small matrix
 //   k_svd     one-sided Jacobi SVD (Hestenes) with the truncation rule
+//   k_norm    spectral norms (Section 5.3)
 //   k_scan    prefix sums of adaptive ranks (panel column offsets)
-// One CTA processes one job; FP64 arithmetic throughout.
+// One CTA processes one job; everything but the contractions of the FP32 and
+// compensated forms is FP64 arithmetic.
 #include <cuda_runtime.h>
 #include <climits>
 #include <math.h>
@@ -39,9 +44,9 @@ __device__ __forceinline__ void set_err(const ExecCtx& x, int code) {
 
 // ------------------------------------------------------------------ GEMM ----
 // Output tile up to GT x GT; the 256 threads are mapped onto the actual output
-// elements (element e = tid + 256 q), so small outputs (16 x 16 coupling and
-// transfer products) waste no FP64 FMA.  Operand chunks of GK columns are
-// staged in shared memory; each output is a dot product over the chunk.
+// elements (see out_map), so small outputs (16 x 16 coupling and transfer
+// products) waste no FP64 FMA.  Operand chunks of GK columns are staged in
+// shared memory; each output is a dot product over the chunk.
 constexpr int GT = 64;
 constexpr int GK = 32;
 constexpr int GQ = (GT * GT) / 256;  // outputs per thread at most
