@@ -1386,6 +1386,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     // per level
     std::vector<int> cl, offslot, wmax;
     std::vector<int64_t> panel, rbuf, ubuf, tbuf, pbuf;
+    std::vector<int> rq;  // rows of the panel's R kept above the noise floor (slot)
   };
   auto make_basis_side = [&](bool rowside) {
     Side S;
@@ -1436,6 +1437,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     S.ubuf.assign(T.ncl, -1);
     S.tbuf.assign(T.ncl, -1);
     S.pbuf.assign(T.ncl, -1);
+    S.rq.assign(T.ncl, -1);
     for (int c : S.cl) {
       std::vector<int> in;
       for (int b : S.star[c]) {
@@ -1493,8 +1495,11 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     for (int c : S.cl) {
       const int n = T.leaf(c) ? T.size[c] : 2 * KP;
       const int nsl = S.offslot[c] + (int)S.star[c].size();  // total width slot
+      // the pivoted QR stops at the SVD's noise floor, as in agglomeration:
+      // the rows of R it drops are columns of R^T the Jacobi SVD would freeze
+      S.rq[c] = B.slot(0);
       B.qr(PT(AR_WS, S.panel[c]), S.wmax[c], DS(nsl), rows_dim(S, c), PT(AR_WS, S.tbuf[c]), PT(AR_WS, S.rbuf[c]), n,
-           0, S.wmax[c], n, PT(AR_WS, S.pbuf[c]));
+           0, S.wmax[c], n, PT(AR_WS, S.pbuf[c]), 0, PARAM_SVD_FLOOR, S.rq[c]);
     }
   };
   // phase 3: Jacobi SVD of R^T with the truncation rule
@@ -1504,9 +1509,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       const int n = T.leaf(c) ? T.size[c] : 2 * KP;
       const Dim rows_d = rows_dim(S, c);
       B.svd_size(n, n);
-      Dim qcols = rows_d;  // M = R^T (rows x q), q = min(rows, panel width)
-      qcols.mc = 0;
-      qcols.ms = S.offslot[c] + (int)S.star[c].size();
+      // M = R^T (rows x r), r <= min(rows, panel width) the rows of R kept
+      const Dim qcols = DS(S.rq[c], 0);
       B.sv.push_back(SvdJob{PT(AR_WS, S.rbuf[c]), PT(AR_WS, S.ubuf[c]), NONE(), n, n, rows_d, qcols, 1, 1, tol_mult,
                             PARAM_TOL_BASIS, S.rank[c], KP, -1, PT(AR_WS, S.pbuf[c])});
     }
