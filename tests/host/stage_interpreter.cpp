@@ -448,6 +448,14 @@ int main(int argc, char** argv) {
     return 4;
   }
   std::printf("stat qr_truncated %ld\n", E.qr_truncated);
+  // largest dynamic shared memory a QR / SVD stage asks for, largest norm n
+  int smem_qr = 0, smem_svd = 0, norm_n = 0;
+  for (const Stage& st : P->stages) {
+    if (st.kind == ST_QR) smem_qr = std::max(smem_qr, st.smem);
+    if (st.kind == ST_SVD) smem_svd = std::max(smem_svd, st.smem);
+    if (st.kind == ST_NORM) norm_n = std::max(norm_n, st.aux);
+  }
+  std::printf("stat smem_max_qr %d\nstat smem_max_svd %d\nstat norm_max_n %d\n", smem_qr, smem_svd, norm_n);
 
   // dense expansion in the caller's ordering
   const BlockTree& BC = *P->cblocks;

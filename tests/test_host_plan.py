@@ -80,6 +80,11 @@ CASES = [
 @pytest.mark.parametrize("w,eps", CASES, ids=[f"{w.name}-{e:g}" for w, e in CASES])
 def test_planned_stages_reproduce_the_oracle(interpreter, tmp_path, w, eps):
     D, ranks, stats = run_interpreter(interpreter, w, eps, tmp_path)
+    # launch limits the kernels are configured for: k_qr 96 KB (128-row TSQR
+    # chunks of 64 columns), k_svd 76 KB (SVD_SMEM_DOUBLES), k_norm n <= 128
+    assert stats["smem_max_qr"] <= 8 * (64 + 128) * 64
+    assert stats["smem_max_svd"] <= 8 * 9732
+    assert stats["norm_max_n"] <= 128
     if w.dim == 3 and w.order == 4:
         assert stats.get("agg_two_step", 0) > 0
         assert stats.get("qr_truncated", 0) > 0
