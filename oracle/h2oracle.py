@@ -24,7 +24,7 @@ structures and no blocking or reordering beyond what the paper states:
   block-relative error control, projection climb and coupling matrices
   (Sections 5.2-5.3).
 
-Readings of points where the paper is silent (each also listed in the design doc):
+Readings of points where the paper is silent:
 
 * R1  ``eta`` here is the factor in  max(diam) <= eta * dist  (eq. (2) with
       2*eta_paper = eta).
@@ -64,6 +64,115 @@ import math
 from dataclasses import dataclass, field
 
 import numpy as np
+
+# --------------------------------------------------------------------------
+# Work counters of the method (measurement only; they change no arithmetic).
+# Every dense operation of the product is counted where it happens:
+#   gemm  a @ b of an (m x k) by a (k x n) matrix: 2 m n k flops
+#   qr    Householder QR of an m x n matrix, R only: 2 n^2 (m - n/3) for
+#         m >= n (2 m^2 (n - m/3) otherwise); forming the thin Q doubles it
+#   svd   thin SVD by the R-SVD operation counts of Golub and Van Loan
+#         (Matrix Computations, Section 8.6): singular values only
+#         2 m n^2 + 2 n^3, with the thin U 6 m n^2 + 11 n^3, with U and V
+#         6 m n^2 + 20 n^3 (m >= n, n <= m by transposition)
+#   norm  spectral norm = the largest singular value (svd count, values only)
+# Bytes: each operation reads its operands and writes its result once
+# (8 bytes per double).  Elementwise sums and scalings (O(k^2) per node
+# against the O(k^3) of the products) are not counted.
+# --------------------------------------------------------------------------
+class Work:
+    KINDS = ("gemm", "qr", "svd", "norm")
+
+    def __init__(self):
+        self.reset()
+
+    def reset(self):
+        self.flops = {k: 0.0 for k in self.KINDS}
+        self.bytes = {k: 0.0 for k in self.KINDS}
+        self.calls = {k: 0 for k in self.KINDS}
+
+    def add(self, kind, flops, nbytes):
+        self.flops[kind] += flops
+        self.bytes[kind] += nbytes
+        self.calls[kind] += 1
+
+    def snapshot(self):
+        return {"flops": dict(self.flops), "bytes": dict(self.bytes), "calls": dict(self.calls)}
+
+
+WORK = Work()
+
+
+def _shape2(a):
+    return (a.shape[0], 1) if a.ndim == 1 else a.shape
+
+
+def mm(a, b):
+    """a @ b, counted as a GEMM."""
+    out = a @ b
+    m, k = _shape2(a)
+    n = 1 if b.ndim == 1 else b.shape[1]
+    WORK.add("gemm", 2.0 * m * n * k, 8.0 * (a.size + b.size + out.size))
+    return out
+
+
+def _qr_flops(m, n):
+    return 2.0 * n * n * (m - n / 3.0) if m >= n else 2.0 * m * m * (n - m / 3.0)
+
+
+def qr_r(a):
+    """R factor of the thin QR of a (counted without forming Q)."""
+    _, r = np.linalg.qr(a)
+    m, n = a.shape
+    WORK.add("qr", _qr_flops(m, n), 8.0 * (a.size + r.size))
+    return r
+
+
+def qr_full(a):
+    """Thin QR a = Q R, counted with the formation of Q."""
+    q, r = np.linalg.qr(a)
+    m, n = a.shape
+    WORK.add("qr", 2.0 * _qr_flops(m, n), 8.0 * (a.size + q.size + r.size))
+    return q, r
+
+
+def _svd_flops(m, n, vectors):
+    if m < n:
+        m, n = n, m
+    if vectors == 0:
+        return 2.0 * m * n * n + 2.0 * n ** 3
+    if vectors == 1:
+        return 6.0 * m * n * n + 11.0 * n ** 3
+    return 6.0 * m * n * n + 20.0 * n ** 3
+
+
+def svd_u(a):
+    """Thin SVD: U, sigma (right singular vectors not used)."""
+    u, sig, _ = np.linalg.svd(a, full_matrices=False)
+    WORK.add("svd", _svd_flops(a.shape[0], a.shape[1], 1), 8.0 * (a.size + u.size + sig.size))
+    return u, sig
+
+
+def svd_uv(a):
+    """Thin SVD: U, sigma, V^*."""
+    u, sig, vh = np.linalg.svd(a, full_matrices=False)
+    WORK.add("svd", _svd_flops(a.shape[0], a.shape[1], 2), 8.0 * (a.size + u.size + sig.size + vh.size))
+    return u, sig, vh
+
+
+def block_norm(g):
+    """Spectral norm ||g||_2 of a condensed block (Section 5.3; computed
+    exactly, reading R13)."""
+    if min(g.shape) == 0:
+        return 0.0
+    WORK.add("norm", _svd_flops(g.shape[0], g.shape[1], 0), 8.0 * g.size)
+    return float(np.linalg.norm(g, 2))
+
+
+def basis_weight(theta, level_s, level_t, nrm):
+    """Weight omega_sr = theta^((level(s) - level(t)) / 2) ||G^c_tr||_2 of a block
+    (t, r) seen at a descendant s of t (Section 5.3)."""
+    return theta ** ((level_s - level_t) / 2.0) * nrm
 
 # --------------------------------------------------------------------------
 # Kernel functions (R5/R6)
@@ -345,7 +454,7 @@ class Basis:
         if c.is_leaf:
             v = self.leaf[c.id]
         else:
-            v = np.vstack([self.full(ch) @ self.trans[ch.id] for ch in c.children])
+            v = np.vstack([mm(self.full(ch), self.trans[ch.id]) for ch in c.children])
         self._full[c.id] = v
         return v
 
@@ -362,7 +471,7 @@ class H2:
         """G|_{t x s} for a block b of the block tree (cluster order)."""
         if b.is_leaf:
             if b.adm:
-                return self.V.full(b.t) @ self.S[id(b)] @ self.W.full(b.s).T
+                return mm(mm(self.V.full(b.t), self.S[id(b)]), self.W.full(b.s).T)
             return self.N[id(b)]
         out = np.zeros((b.t.size, b.s.size))
         for c in b.children:
@@ -458,12 +567,12 @@ def basis_products(WX, VY, root):
 
     def rec(s):
         if s.is_leaf:
-            P[s.id] = WX.leaf[s.id].T @ VY.leaf[s.id]
+            P[s.id] = mm(WX.leaf[s.id].T, VY.leaf[s.id])
         else:
             acc = np.zeros((WX.rank[s.id], VY.rank[s.id]))
             for ch in s.children:
                 rec(ch)
-                acc += WX.trans[ch.id].T @ P[ch.id] @ VY.trans[ch.id]
+                acc += mm(mm(WX.trans[ch.id].T, P[ch.id]), VY.trans[ch.id])
             P[s.id] = acc
     rec(root)
     return P
@@ -478,7 +587,7 @@ def _mm(a, b):
         return b
     if b is None:
         return a
-    return a @ b
+    return mm(a, b)
 
 
 class BT:
@@ -503,10 +612,10 @@ def bt_yield(a, basis):
     """Def. 9."""
     t = a.t
     if t.is_leaf:
-        return _mm(basis.full(t) @ a.C + a.N, a.M)
+        return _mm(mm(basis.full(t), a.C) + a.N, a.M)
     if a.kids is None:
-        return _mm(basis.full(t) @ a.C, a.M)
-    rows = [basis.full(tc) @ (basis.trans[tc.id] @ a.C) + bt_yield(ac, basis)
+        return _mm(mm(basis.full(t), a.C), a.M)
+    rows = [mm(basis.full(tc), mm(basis.trans[tc.id], a.C)) + bt_yield(ac, basis)
             for tc, ac in zip(t.children, a.kids)]
     return _mm(np.vstack(rows), a.M)
 
@@ -523,10 +632,10 @@ def bt_finish(a):
     if a.M is None:
         return a
     if a.t.is_leaf:
-        return BT(a.t, a.C @ a.M, None, a.N @ a.M)
+        return BT(a.t, mm(a.C, a.M), None, mm(a.N, a.M))
     if a.kids is None:
-        return BT(a.t, a.C @ a.M)
-    return BT(a.t, a.C @ a.M, None, None, [bt_mul(c, a.M) for c in a.kids])
+        return BT(a.t, mm(a.C, a.M))
+    return BT(a.t, mm(a.C, a.M), None, None, [bt_mul(c, a.M) for c in a.kids])
 
 
 def bt_split(a, basis):
@@ -535,7 +644,7 @@ def bt_split(a, basis):
     CM = _mm(a.C, a.M)
     kids = []
     for tc in t.children:
-        c = basis.trans[tc.id] @ CM
+        c = mm(basis.trans[tc.id], CM)
         kids.append(BT(tc, c, None, np.zeros((tc.size, c.shape[1]))) if tc.is_leaf else BT(tc, c))
     return BT(t, np.zeros((a.C.shape[0], CM.shape[1])), None, None, kids)
 
@@ -571,7 +680,7 @@ def bt_nearfield(t, Z, krow):
 def bt_restrict(a, tc, basis):
     """Restriction of yield(alpha) to the rows of a child tc (Section 4.3)."""
     CM = _mm(a.C, a.M)
-    push = basis.trans[tc.id] @ CM
+    push = mm(basis.trans[tc.id], CM)
     if a.kids is None:
         if tc.is_leaf:
             return BT(tc, push, None, np.zeros((tc.size, push.shape[1])))
@@ -621,10 +730,10 @@ def addproduct(side, b, S, a):
     Z the side's matrix (X or Y^*), U its partner basis (V_Y or W_X)."""
     t, s = side.row(b), side.col(b)
     if b.is_leaf and b.adm:
-        beta = bt_uniform(t, side.coupling(b) @ side.Pmat(s) @ S)
+        beta = bt_uniform(t, mm(mm(side.coupling(b), side.Pmat(s)), S))
         return bt_add(a, beta, side.basis)
     if b.is_leaf:
-        Z = side.near(b) @ (side.descend_basis.full(s) @ S)
+        Z = mm(side.near(b), mm(side.descend_basis.full(s), S))
         beta = bt_nearfield(t, Z, a.C.shape[0])
         return bt_add(a, beta, side.basis)
     # subdivided block: make alpha split and finished, recurse into children (R7)
@@ -633,7 +742,7 @@ def addproduct(side, b, S, a):
         a = bt_split(a, side.basis)
     kids = list(a.kids) if a.kids is not None else None
     for tc, sc, c in side.children(b):
-        Sc = S if sc is s else side.descend_basis.trans[sc.id] @ S
+        Sc = S if sc is s else mm(side.descend_basis.trans[sc.id], S)
         if tc is t:
             a = addproduct(side, c, Sc, a)
             kids = list(a.kids) if a.kids is not None else None
@@ -680,7 +789,7 @@ class Product:
         elif xb.is_leaf and xb.adm:                     # case 2
             acc.beta = addproduct(self.sideB, yb, self.X.S[id(xb)].T, acc.beta)
         elif xb.is_leaf or yb.is_leaf:                  # case 3
-            prod = self.X.dense_block(xb) @ self.Y.dense_block(yb)
+            prod = mm(self.X.dense_block(xb), self.Y.dense_block(yb))
             acc.N = prod if acc.N is None else acc.N + prod
         else:                                           # case 4
             acc.P.append((xb, yb))
@@ -719,12 +828,12 @@ class Product:
         L = np.hstack([A, self.X.V.full(acc.t)])
         R = np.hstack([self.Y.W.full(acc.r), B])
         if acc.N is not None:
-            return (L @ R.T + acc.N, np.eye(acc.r.size))
+            return (mm(L, R.T) + acc.N, np.eye(acc.r.size))
         return (L, R)
 
     def dense(self, acc):
         L, R = self.factor(acc)
-        return L @ R.T
+        return mm(L, R.T)
 
 
 def split_pairs(t, r):
@@ -746,13 +855,13 @@ def merge_columns(f1, f2, eps, eps_is_zero):
     """Agglomerate [L1 R1^*, L2 R2^*] (same rows): QR of the block-diagonal
     right factor, condensed matrix, SVD, truncation."""
     (L1, R1), (L2, R2) = f1, f2
-    Q1, r1 = np.linalg.qr(R1)
-    Q2, r2 = np.linalg.qr(R2)
-    G = np.hstack([L1 @ r1.T, L2 @ r2.T])
-    U, sig, Vh = np.linalg.svd(G, full_matrices=False)
+    Q1, r1 = qr_full(R1)
+    Q2, r2 = qr_full(R2)
+    G = np.hstack([mm(L1, r1.T), mm(L2, r2.T)])
+    U, sig, Vh = svd_uv(G)
     k = _truncate(sig, eps, eps_is_zero)
     Vk = Vh[:k].T
-    Qv = np.vstack([Q1 @ Vk[:Q1.shape[1]], Q2 @ Vk[Q1.shape[1]:]])
+    Qv = np.vstack([mm(Q1, Vk[:Q1.shape[1]]), mm(Q2, Vk[Q1.shape[1]:])])
     return (U[:, :k] * sig[:k], Qv)
 
 
@@ -760,12 +869,12 @@ def merge_rows(f1, f2, eps, eps_is_zero):
     """Agglomerate [L1 R1^*; L2 R2^*] (same columns): QR of [R1 R2],
     condensed [L1 r_1^*; L2 r_2^*], SVD, truncation (Section 5.1)."""
     (L1, R1), (L2, R2) = f1, f2
-    Q, r = np.linalg.qr(np.hstack([R1, R2]))
+    Q, r = qr_full(np.hstack([R1, R2]))
     m1 = R1.shape[1]
-    G = np.vstack([L1 @ r[:, :m1].T, L2 @ r[:, m1:].T])
-    U, sig, Vh = np.linalg.svd(G, full_matrices=False)
+    G = np.vstack([mm(L1, r[:, :m1].T), mm(L2, r[:, m1:].T)])
+    U, sig, Vh = svd_uv(G)
     k = _truncate(sig, eps, eps_is_zero)
-    return (U[:, :k] * sig[:k], Q @ Vh[:k].T)
+    return (U[:, :k] * sig[:k], mm(Q, Vh[:k].T))
 
 
 # --------------------------------------------------------------------------
@@ -789,6 +898,7 @@ def multiply(X, Y, eps, theta=0.25):
     eps_is_zero = eps == 0.0
     eps_c = eps / 3.0
     eps_side = eps / 4.0
+    WORK.reset()
     prod = Product(X, Y)
     tI, tK = X.rows, Y.cols
     target = build_block_tree(tI, tK, X.eta)
@@ -861,11 +971,11 @@ def multiply(X, Y, eps, theta=0.25):
     Gc, Gcc, norms = {}, {}, {}
     for b in adm:
         L, R = factors[id(b)]
-        _, Rr = np.linalg.qr(R)            # B_tr = Q_tr R_tr
-        Gc[id(b)] = L @ Rr.T               # condensed G^c_tr
-        _, Rl = np.linalg.qr(L)            # adjoint: A_tr = Q' R'
-        Gcc[id(b)] = R @ Rl.T
-        norms[id(b)] = np.linalg.norm(Gc[id(b)], 2) if min(Gc[id(b)].shape) > 0 else 0.0
+        Rr = qr_r(R)                       # B_tr = Q_tr R_tr
+        Gc[id(b)] = mm(L, Rr.T)            # condensed G^c_tr
+        Rl = qr_r(L)                       # adjoint: A_tr = Q' R'
+        Gcc[id(b)] = mm(R, Rl.T)
+        norms[id(b)] = block_norm(Gc[id(b)])
 
     def build_basis(root, blocks_of, cond, cluster_of):
         """Weighted adaptive cluster basis (Sections 5.2-5.3), bottom-up."""
@@ -889,7 +999,7 @@ def multiply(X, Y, eps, theta=0.25):
                 if nb == 0.0:
                     continue
                 tb = cluster_of(b)
-                w = theta ** ((c.level - tb.level) / 2.0) * nb
+                w = basis_weight(theta, c.level, tb.level, nb)
                 if c.is_leaf:
                     ro = c.off - tb.off
                     blk = cond[id(b)][ro:ro + c.size]
@@ -900,7 +1010,7 @@ def multiply(X, Y, eps, theta=0.25):
             nrows = c.size if c.is_leaf else sum(rank[ch.id] for ch in c.children)
             if cols:
                 G = np.hstack(cols)
-                U, sig, _ = np.linalg.svd(G, full_matrices=False)
+                U, sig = svd_u(G)
                 k = len(sig) if eps_is_zero else int(np.sum(sig > tol))
                 Vh = U[:, :k]
             else:
@@ -914,7 +1024,7 @@ def multiply(X, Y, eps, theta=0.25):
                     trans[ch.id] = Vh[o:o + rank[ch.id]]
                     o += rank[ch.id]
             for b, blk in keys:
-                ghat[(c.id, id(b))] = Vh.T @ blk
+                ghat[(c.id, id(b))] = mm(Vh.T, blk)
         rec(root)
         return Basis(root, leaf, trans, rank)
 
@@ -928,12 +1038,13 @@ def multiply(X, Y, eps, theta=0.25):
     S, N = {}, {}
     for b in adm:
         L, R = factors[id(b)]
-        S[id(b)] = (Vnew.full(b.t).T @ L) @ (Wnew.full(b.s).T @ R).T
+        S[id(b)] = mm(mm(Vnew.full(b.t).T, L), mm(Wnew.full(b.s).T, R).T)
     for b in block_leaves(target):
         if not b.adm:
             N[id(b)] = dense_out[id(b)]
     C = H2(tI, tK, target, Vnew, Wnew, S, N)
     C.eta = X.eta
+    stats["work"] = WORK.snapshot()
     return MulResult(C, factors, Vnew.rank, Wnew.rank, norms, stats["agglomerated"], stats)
 
 

@@ -353,3 +353,217 @@ def test_planted_mistake_is_caught(monkeypatch):
     res = O.multiply(X, Y, 0.0)
     Z = X.dense() @ Y.dense()
     assert max(e for e, _ in block_rel_errors(res.C, Z)) > 1e-6
+
+
+# ------------------------------------------------------ kernel functions ----
+# Hand-computed values: ln 5 = 1.6094379124341003, ln 3 = 1.0986122886681098,
+# ln 2 = 0.6931471805599453, e^-2.5 = 0.0820849986238988,
+# e^-5 = 0.006737946999085467, e^-3 = 0.049787068367863944,
+# 1/(2 pi) = 0.15915494309189535.
+@pytest.mark.parametrize("spec,x,y,value", [
+    (I.LOG, (0.0, 0.0), (3.0, 4.0), -1.6094379124341003),               # -log 5
+    (I.LOG_2PI, (0.0, 0.0), (3.0, 4.0), -1.6094379124341003 * 0.15915494309189535),
+    (I.LOG, (0.25,), (0.75,), 0.6931471805599453),                       # -log 0.5
+    (I.LOG, (1.0, 2.0, 2.0), (0.0, 0.0, 0.0), -1.0986122886681098),     # -log 3
+    (I.INV, (0.0, 0.0), (3.0, 4.0), 0.2),
+    (I.INV, (1.0, 2.0, 2.0), (0.0, 0.0, 0.0), 1.0 / 3.0),
+    (I.INV_4PI, (0.0, 0.0, 0.0), (0.0, 0.3, 0.4), 0.15915494309189535),  # 1/(4 pi 0.5)
+    (I.GAUSS_01, (0.0, 0.0), (0.3, 0.4), 0.0820849986238988),            # exp(-0.25/0.1)
+    (I.EXP, (0.0, 0.0), (3.0, 4.0), 0.006737946999085467),               # exp(-5)
+    (I.EXP, (1.0, 2.0, 2.0), (0.0, 0.0, 0.0), 0.049787068367863944),    # exp(-3)
+], ids=["log-r5", "log2pi-r5", "log-1d", "log-3d", "inv-r5", "inv-3d", "inv4pi", "gauss", "exp-r5", "exp-3d"])
+def test_kernel_closed_forms(spec, x, y, value):
+    """R5/R6: each kernel string of the workloads, evaluated at point pairs
+    whose distance is known (the Pythagorean triples 3-4-5 and 1-2-2-3)."""
+    g = O.kernel_eval(spec.kind, spec.kparam(), np.array([x]), np.array([y]))
+    assert g.shape == (1, 1)
+    assert g[0, 0] == pytest.approx(value, rel=1e-14, abs=0.0)
+    # symmetric in its arguments
+    assert O.kernel_eval(spec.kind, spec.kparam(), np.array([y]), np.array([x]))[0, 0] == g[0, 0]
+
+
+@pytest.mark.parametrize("spec,diag", [(I.LOG, 1.0), (I.LOG_2PI, 1.0), (I.INV_4PI, 0.0), (I.INV, 0.0),
+                                       (I.GAUSS_01, 1.0), (I.EXP, 1.0)])
+def test_kernel_diagonal_rule(spec, diag):
+    """R5: the Nystroem entry i == j takes the workload's diagonal value; off
+    the diagonal the kernel is evaluated (here at distance 5 on a 3-4-5 pair)."""
+    pts = np.array([[0.0, 0.0], [3.0, 4.0]])
+    g = O.kernel_block(spec.kind, spec.kparam(), pts, np.arange(2), np.arange(2))
+    assert g[0, 0] == diag and g[1, 1] == diag
+    off = O.kernel_eval(spec.kind, spec.kparam(), pts[:1], pts[1:])[0, 0]
+    assert g[0, 1] == off and g[1, 0] == off
+
+
+# ------------------------------------------------ weighted recompression ----
+THETA = 0.25
+
+
+def _adm_blocks(res):
+    return [b for b in O.block_leaves(res.C.blocks) if b.adm]
+
+
+def _dense_factor(res, b):
+    L, R = res.factors[id(b)]
+    return L @ R.T
+
+
+def _ancestors_or_self(c):
+    out = []
+    while c is not None:
+        out.append(c)
+        c = c.parent
+    return out
+
+
+def _basis_discrepancy(res, eps, row_side, leaves_only=False):
+    """Sections 5.2-5.3, rebuilt by this test from the blocks before
+    recompression and the oracle's output bases.  For every cluster t the
+    weighted stacked matrix
+        G_t = [ H_b / omega_{t,b} ]_b,   b = (t', r) admissible, t' = t or an
+        ancestor of t,  omega = theta^((level t - level t')/2) ||G_b||_2,
+    with H_b = G_b|_t for a leaf and H_b = [V_{t1}^* G_b|_{t1}; V_{t2}^* G_b|_{t2}]
+    (the children's output bases) otherwise, must satisfy
+        ||G_t - Vh_t Vh_t^* G_t||_2 = sigma_{k+1}(G_t)
+    where Vh_t is the leaf basis V_t or the stacked transfer matrices
+    [E_{t1}; E_{t2}] and k its rank, with the rank decision
+    sigma_{k+1} <= tol < sigma_k, tol = (eps/4) sqrt(1 - 2 theta).  The blocks
+    are used uncondensed: a right isometry changes neither singular values nor
+    left singular vectors.  Returns the largest violation relative to sigma_1."""
+    tol = (eps / 4.0) * math.sqrt(1.0 - 2.0 * THETA)
+    basis = res.C.V if row_side else res.C.W
+    root = res.C.rows if row_side else res.C.cols
+    blocks_at, dense, nrm = {}, {}, {}
+    for b in _adm_blocks(res):
+        c = b.t if row_side else b.s
+        blocks_at.setdefault(c.id, []).append(b)
+        G = _dense_factor(res, b)
+        dense[id(b)] = G if row_side else G.T
+        nrm[id(b)] = np.linalg.svd(G, compute_uv=False)[0]
+    worst = 0.0
+    clusters = O.leaves_of(root) if leaves_only else O.all_clusters(root)
+    for t in clusters:
+        cols = []
+        for anc in _ancestors_or_self(t):
+            for b in blocks_at.get(anc.id, []):
+                if nrm[id(b)] == 0.0:
+                    continue
+                G = dense[id(b)]
+                w = THETA ** ((t.level - anc.level) / 2.0) * nrm[id(b)]
+                if t.is_leaf:
+                    ro = t.off - anc.off
+                    H = G[ro:ro + t.size]
+                else:
+                    parts = []
+                    for ch in t.children:
+                        ro = ch.off - anc.off
+                        parts.append(basis.full(ch).T @ G[ro:ro + ch.size])
+                    H = np.vstack(parts)
+                cols.append(H / w)
+        if t.is_leaf:
+            Vh = basis.leaf[t.id]
+        else:
+            Vh = np.vstack([basis.trans[ch.id] for ch in t.children])
+        if not cols:
+            assert Vh.shape[1] == 0
+            continue
+        Gt = np.hstack(cols)
+        sig = np.linalg.svd(Gt, compute_uv=False)
+        k = Vh.shape[1]
+        dropped = sig[k] if k < len(sig) else 0.0
+        err = np.linalg.norm(Gt - Vh @ (Vh.T @ Gt), 2)
+        viol = abs(err - dropped) / sig[0]
+        if dropped > tol * (1 + 1e-9):
+            viol = max(viol, (dropped - tol) / sig[0])
+        if k > 0 and sig[k - 1] <= tol * (1 - 1e-9):
+            viol = max(viol, (tol - sig[k - 1]) / sig[0])
+        worst = max(worst, viol)
+    return worst
+
+
+@pytest.fixture(scope="module")
+def grid_products():
+    out = {}
+    for eps in (1e-4, 1e-6):
+        w = I.grid_2d(32, eps)
+        X, Y = build_pair(w)
+        out[eps] = (X, Y, O.multiply(X, Y, eps))
+    return out
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_weighted_blockwise_basis_bound(grid_products, eps):
+    """Section 5.3: with the weights omega and tol = (eps/4) sqrt(1 - 2 theta),
+    every admissible block b = (t, r) keeps
+        ||G_b - V_t V_t^* G_b||_2 <= (eps/4) ||G_b||_2   (row basis)
+        ||G_b - G_b W_r W_r^*||_2 <= (eps/4) ||G_b||_2   (column basis)
+    with G_b the accumulated (or agglomerated) block before recompression."""
+    _, _, res = grid_products[eps]
+    worst_row = worst_col = 0.0
+    for b in _adm_blocks(res):
+        G = _dense_factor(res, b)
+        nrm = np.linalg.svd(G, compute_uv=False)[0]
+        V, W = res.C.V.full(b.t), res.C.W.full(b.s)
+        er = np.linalg.norm(G - V @ (V.T @ G), 2) / nrm
+        ec = np.linalg.norm(G - (G @ W) @ W.T, 2) / nrm
+        assert er <= (eps / 4.0) * (1 + 1e-9)
+        assert ec <= (eps / 4.0) * (1 + 1e-9)
+        worst_row, worst_col = max(worst_row, er), max(worst_col, ec)
+    # the bound is attained to within a small factor: the truncation is active
+    assert worst_row > 0.02 * eps / 4.0 and worst_col > 0.02 * eps / 4.0
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+@pytest.mark.parametrize("row_side", [True, False], ids=["rows", "cols"])
+def test_basis_error_is_largest_dropped_weighted_sigma(grid_products, eps, row_side):
+    """Section 5.2: ||G_t - V_t V_t^* G_t||_2 = sigma_{k+1} for the weighted
+    stacked matrix of every cluster (leaf bases and nested transfer matrices),
+    with the rank chosen against tol (Section 5.3)."""
+    _, _, res = grid_products[eps]
+    # the equality holds to rounding (~1e-17 sigma_1); a planted weight
+    # mistake misses it by 1e-12 sigma_1 or more (next test)
+    assert _basis_discrepancy(res, eps, row_side) < 1e-13
+
+
+def test_planted_weight_mistakes_are_caught(monkeypatch):
+    """A wrong weight exponent sign, or the Frobenius norm in place of the
+    spectral norm, must break the basis pin."""
+    eps = 1e-2
+    w = I.grid_2d(32, eps)
+    X, Y = build_pair(w)
+    assert _basis_discrepancy(O.multiply(X, Y, eps), eps, True) < 1e-13
+    good = O.basis_weight
+    monkeypatch.setattr(O, "basis_weight", lambda th, ls, lt, nrm: good(th, lt, ls, nrm))
+    assert _basis_discrepancy(O.multiply(X, Y, eps), eps, True) > 1e-11
+    monkeypatch.setattr(O, "basis_weight", good)
+    monkeypatch.setattr(O, "block_norm", lambda g: float(np.linalg.norm(g)) if g.size else 0.0)
+    assert _basis_discrepancy(O.multiply(X, Y, eps), eps, True) > 1e-11
+
+
+# ------------------------------------------------------ work counters ----
+def test_work_counters_count_the_operations():
+    """The counters of the oracle: a GEMM of (m x k)(k x n) is 2mnk flops and
+    reads/writes its three matrices; QR and SVD follow the stated formulas."""
+    O.WORK.reset()
+    a, b = np.ones((3, 5)), np.ones((5, 7))
+    O.mm(a, b)
+    assert O.WORK.flops["gemm"] == 2 * 3 * 5 * 7
+    assert O.WORK.bytes["gemm"] == 8 * (15 + 35 + 21)
+    O.qr_r(np.ones((10, 4)))
+    assert O.WORK.flops["qr"] == pytest.approx(2 * 16 * (10 - 4 / 3))
+    O.svd_u(np.ones((4, 10)))
+    assert O.WORK.flops["svd"] == pytest.approx(6 * 10 * 16 + 11 * 64)
+
+
+def test_work_grows_like_n_log_n():
+    """Section 4 / Section 6: the work of a product grows like n k^2 log n at
+    fixed k; doubling n on the 1D workload multiplies it by about
+    2 (log 2n / log n), well below 4."""
+    fl = []
+    for n in (512, 1024, 2048):
+        w = I.plain_1d(n, 1e-6)
+        X, Y = build_pair(w)
+        res = O.multiply(X, Y, w.eps)
+        wk = res.stats["work"]
+        fl.append(sum(wk["flops"].values()))
+        assert wk["calls"]["gemm"] > 0 and wk["calls"]["qr"] > 0 and wk["calls"]["svd"] > 0
+    assert 1.6 < fl[1] / fl[0] < 3.0 and 1.6 < fl[2] / fl[1] < 3.0
