@@ -1,10 +1,11 @@
 // h2_matvec_noalloc: an H^2 matrix-vector product that allocates nothing.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation is not a capturable operation),
-// latency-critical loops that must not enter the allocator, and hosts whose
-// device memory is partitioned up front.  This entry point serves them.  Its
-// intermediate coefficient vectors x^_s = W_s^* x|_s and y^_t live in one
+// Some callers cannot call cudaMalloc: latency-critical loops that must not
+// enter the allocator (an allocation can synchronise the device or wait on
+// the driver), and processes whose device memory is partitioned up front
+// (an allocator owned by another component, or a fixed memory budget that
+// leaves no room for further allocations).  This entry point serves them.
+// Its intermediate coefficient vectors x^_s = W_s^* x|_s and y^_t live in one
 // file-scope device array of fixed size; the block lists of the matrix travel
 // as kernel parameters, so no schedule has to be uploaded either.
 //
@@ -84,6 +85,8 @@ __global__ void k_nf_fwd_up(NfMat M, int level, double* xh) {
 
 constexpr int NF_MAXE = 1536;  // block entries per parameter chunk (24 KB of kernel parameters)
 
+// Block entries of one launch, sorted by row cluster t (stable, so the
+// entries of one t keep the order of the matrix's block lists).
 struct NfChunk {
   int count;
   int t[NF_MAXE];
@@ -91,14 +94,21 @@ struct NfChunk {
   int64_t off[NF_MAXE];  // coupling (k x k) or nearfield block offset in the arena
 };
 
-// y^_t += sum S_ts x^_s over the chunk's blocks of row cluster t = blockIdx.x
-// (one CTA per cluster scans the chunk: deterministic order, no atomics)
+// CTA e handles the run of entries that starts at e (entries e' >= e with the
+// same t); CTAs whose entry is not the first of its run return at once.  The
+// work is proportional to the blocks, the order fixed, and no atomics.
+__device__ __forceinline__ bool nf_run_start(const NfChunk& C, int e) {
+  return e < C.count && (e == 0 || C.t[e - 1] != C.t[e]);
+}
+
+// y^_t += sum S_ts x^_s over the chunk's run of blocks of row cluster t
 __global__ void k_nf_couple(NfMat M, const __grid_constant__ NfChunk C, const double* xh, double* yh) {
-  const int t = blockIdx.x;
+  const int e0 = blockIdx.x;
+  if (!nf_run_start(C, e0)) return;
+  const int t = C.t[e0];
   for (int i = threadIdx.x; i < M.k; i += blockDim.x) {
     double s = yh[(int64_t)t * M.k + i];
-    for (int e = 0; e < C.count; ++e) {
-      if (C.t[e] != t) continue;
+    for (int e = e0; e < C.count && C.t[e] == t; ++e) {
       const double* S = M.a + C.off[e];
       const double* xs = xh + (int64_t)C.s[e] * M.k;
       for (int j = 0; j < M.k; ++j) s = fma(S[(int64_t)i * M.k + j], xs[j], s);
@@ -131,15 +141,16 @@ __global__ void k_nf_leaf(NfMat M, const double* yh, double* y) {
   }
 }
 
-// y|_t += sum N_ts x|_s over the chunk's blocks of leaf t = first leaf + blockIdx.x
+// y|_t += sum N_ts x|_s over the chunk's run of blocks of leaf t
 __global__ void k_nf_near(NfMat M, const __grid_constant__ NfChunk C, const double* x, double* y) {
-  const int t = ((1 << M.depth) - 1) + blockIdx.x;
+  const int e0 = blockIdx.x;
+  if (!nf_run_start(C, e0)) return;
+  const int t = C.t[e0];
   int to, ts;
   cluster_range(t, M.n, to, ts);
   for (int r = threadIdx.x; r < ts; r += blockDim.x) {
     double s = y[to + r];
-    for (int e = 0; e < C.count; ++e) {
-      if (C.t[e] != t) continue;
+    for (int e = e0; e < C.count && C.t[e] == t; ++e) {
       int so, ss;
       cluster_range(C.s[e], M.n, so, ss);
       const double* N = M.a + C.off[e];
@@ -153,6 +164,38 @@ constexpr int NF_MAXDEV = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[NF_MAXDEV] = {};  // per device, set up once
 
+// True when p is device (or managed) memory that device dev can address as
+// its own.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
+// Host staging of the kernel parameters: static storage (no allocation, not
+// thread-local), used under g_noalloc_mu.  Kernel parameters are copied at
+// launch, so the buffers are free again once a launch call returns.
+NfChunk g_chunk, g_sorted;
+uint64_t g_keys[NF_MAXE];
+
+// Entries of g_chunk sorted by row cluster into g_sorted, insertion order kept
+// within a cluster: an in-place sort of the keys (t, position).
+void sort_chunk() {
+  const NfChunk& C = g_chunk;
+  for (int e = 0; e < C.count; ++e) g_keys[e] = ((uint64_t)(uint32_t)C.t[e] << 32) | (uint32_t)e;
+  std::sort(g_keys, g_keys + C.count);
+  g_sorted.count = C.count;
+  for (int e = 0; e < C.count; ++e) {
+    const int i = (int)(g_keys[e] & 0xffffffffu);
+    g_sorted.t[e] = C.t[i];
+    g_sorted.s[e] = C.s[i];
+    g_sorted.off[e] = C.off[i];
+  }
+}
+
 }  // namespace
 }  // namespace h2
 
@@ -164,32 +207,43 @@ extern "C" int h2_matvec_noalloc(const h2_matrix* A, const double* x, double* y,
   const int k = A->kpad;
   if (A->cols.get() != A->rows.get() && (A->cols->n != R.n || A->cols->depth != R.depth)) return H2_EINVAL;
   if (2 * (int64_t)R.ncl * k > NOALLOC_SCRATCH_DOUBLES) return H2_ENOMEM;  // beyond the static scratch
+  cudaGetLastError();  // an error left by an earlier, unrelated call is not this call's
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= NF_MAXDEV) return H2_ECUDA;
-  double* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      // once per device, with that device current: device address of the
-      // static array (its host-side name is only a stand-in)
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return H2_ECUDA;
-      g_noalloc_ptr[dev] = (double*)p;
-    }
-    scratch = g_noalloc_ptr[dev];
+  // the matrix and both vectors must live on the current device
+  if (!on_device(A->d_arena, dev) || !on_device(x, dev) || !on_device(y, dev)) return H2_EINVAL;
+  // one caller at a time on the host: the parameter staging buffers are shared
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    // once per device, with that device current: device address of the
+    // static array (its host-side name is only a stand-in)
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return H2_ECUDA;
+    g_noalloc_ptr[dev] = (double*)p;
   }
-  if (A->done && cudaEventSynchronize(A->done) != cudaSuccess) return H2_ECUDA;
+  double* scratch = g_noalloc_ptr[dev];
   cudaStream_t st = (cudaStream_t)stream;
+  // a product still in flight: order the reads after it on the device (no host wait)
+  if (A->done && cudaStreamWaitEvent(st, A->done, 0) != cudaSuccess) return H2_ECUDA;
+#define NF_CHECK()                                          \
+  do {                                                      \
+    if (cudaGetLastError() != cudaSuccess) return H2_ECUDA; \
+  } while (0)
   const NfMat M{A->d_arena, A->off_V, A->off_E, A->off_W, A->off_F, A->off_S, A->off_N, R.n, R.depth, k};
   double* xh = scratch;
   double* yh = scratch + (int64_t)R.ncl * k;
   const int D = R.depth;
   // the scratch keeps the previous call's contents: y^ must start at zero
   k_nf_zero<<<64, 256, 0, st>>>(yh, (int64_t)R.ncl * k);
+  NF_CHECK();
   k_nf_fwd_leaf<<<1 << D, 64, 0, st>>>(M, x, xh);
-  for (int l = D - 1; l >= 0; --l) k_nf_fwd_up<<<1 << l, 64, 0, st>>>(M, l, xh);
+  NF_CHECK();
+  for (int l = D - 1; l >= 0; --l) {
+    k_nf_fwd_up<<<1 << l, 64, 0, st>>>(M, l, xh);
+    NF_CHECK();
+  }
   const BlockTree& B = *A->blocks;
-  static thread_local NfChunk C;  // parameters staged on the host, no allocation
+  NfChunk& C = g_chunk;
   for (size_t i0 = 0; i0 < B.adm_list.size(); i0 += NF_MAXE) {
     C.count = (int)std::min<size_t>(NF_MAXE, B.adm_list.size() - i0);
     for (int e = 0; e < C.count; ++e) {
@@ -198,10 +252,16 @@ extern "C" int h2_matvec_noalloc(const h2_matrix* A, const double* x, double* y,
       C.s[e] = B.s[b];
       C.off[e] = A->off_S + (int64_t)(i0 + e) * k * k;
     }
-    k_nf_couple<<<R.ncl, 64, 0, st>>>(M, C, xh, yh);
+    sort_chunk();
+    k_nf_couple<<<C.count, 64, 0, st>>>(M, g_sorted, xh, yh);
+    NF_CHECK();
   }
-  for (int l = 1; l <= D; ++l) k_nf_bwd<<<1 << l, 64, 0, st>>>(M, l, yh);
+  for (int l = 1; l <= D; ++l) {
+    k_nf_bwd<<<1 << l, 64, 0, st>>>(M, l, yh);
+    NF_CHECK();
+  }
   k_nf_leaf<<<1 << D, 128, 0, st>>>(M, yh, y);
+  NF_CHECK();
   for (size_t i0 = 0; i0 < B.inadm_list.size(); i0 += NF_MAXE) {
     C.count = (int)std::min<size_t>(NF_MAXE, B.inadm_list.size() - i0);
     for (int e = 0; e < C.count; ++e) {
@@ -210,7 +270,10 @@ extern "C" int h2_matvec_noalloc(const h2_matrix* A, const double* x, double* y,
       C.s[e] = B.s[b];
       C.off[e] = A->off_N + B.near_off[i0 + e];
     }
-    k_nf_near<<<1 << D, 128, 0, st>>>(M, C, x, y);
+    sort_chunk();
+    k_nf_near<<<C.count, 128, 0, st>>>(M, g_sorted, x, y);
+    NF_CHECK();
   }
-  return cudaGetLastError() == cudaSuccess ? H2_OK : H2_ECUDA;
+#undef NF_CHECK
+  return H2_OK;
 }

@@ -1,8 +1,9 @@
 """h2_matvec_noalloc: the allocation-free matrix-vector product (for callers
-that cannot call cudaMalloc, e.g. code enqueued inside a CUDA stream capture)
-must give the same y as h2_matvec, call after call.  Its scratch is a static
-device array shared by all calls, so two calls in a row must not see each
-other's leftovers.  This file is collected last on purpose."""
+that cannot call cudaMalloc: loops that must stay out of the allocator, or
+processes whose device memory is partitioned up front) must give the same y
+as h2_matvec, call after call.  Its scratch is a static device array shared
+by all calls, so two calls in a row must not see each other's leftovers.
+This file is collected last on purpose."""
 import ctypes as C
 
 import numpy as np
@@ -45,3 +46,32 @@ def test_noalloc_matvec_matches_h2_matvec(w):
             ref = y_ref[perm]
             assert np.all(np.isfinite(y))
             assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_noalloc_rejects_trees_beyond_its_scratch():
+    """A matrix whose coefficient vectors (2 * nclusters * kpad doubles) do not
+    fit the fixed 2^20-double scratch is refused with H2_ENOMEM before any
+    device work: 1D, order 8 (k = 8), leaf 2, n = 131072 has 131071 clusters."""
+    n = 131072
+    pts = I.uniform_points(n, 1, 77)
+    M = h2.build(pts, I.LOG, 2.0, 2, 8)
+    st = M.info()
+    assert 2 * st.nclusters * st.kpad > (1 << 20)
+    lib = h2._lib()
+    lib.h2_matvec_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    rc = lib.h2_matvec_noalloc(M.handle, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), None)
+    assert rc == h2.H2_ENOMEM
+
+
+def test_noalloc_rejects_host_vectors():
+    """x and y must be device memory of the current device."""
+    w = I.plain_1d(256)
+    M = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
+    lib = h2._lib()
+    lib.h2_matvec_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    xh = np.zeros(w.n)
+    yd = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    rc = lib.h2_matvec_noalloc(M.handle, C.c_void_p(xh.ctypes.data), C.c_void_p(yd.data_ptr()), None)
+    assert rc == h2.H2_EINVAL
