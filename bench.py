@@ -3,7 +3,15 @@
 Workload (one step = one product C = A*B through h2_mul, inputs resident in
 HBM): 128 x 128 grid on the unit square (n = 16384), A = -log|x-y|/(2 pi)
 (diagonal 1), B = exp(-|x-y|^2/0.1), leaf size 64, eta 2, tensor Chebyshev
-order 4 (k = 16), FP64 throughout (the plain form; no other form exists yet).
+order 4 (k = 16).  `value` is the plain FP64 form timed with CUDA events;
+`chosen_form` is the served, mixed-precision form (continuous batching over
+streams with compensated contractions), timed beside it.
+
+Roofline: the algorithmic work of one product is the one counted by the CPU
+oracle's counters (tests/golden/work_counts.json, written from the oracle
+alone); the dominant kernel kind's share of it over that kind's measured time
+gives `achieved`.  The work the GPU kernels execute (their own counts) is
+reported beside it.
 
 Prints one JSON line (rank 0).  Multi-GPU (torchrun): independent replicas,
 one per GPU, no collective on the data path ("scaling": "weak").
@@ -39,6 +47,25 @@ def workload_config(grid=GRID):
         "n": grid * grid, "k": 16, "leaf_size": 64, "eta": 2.0, "eps": EPS, "form": "plain FP64",
         "l2": "flushed between timed steps (256 MiB write)",
     }
+
+
+def load_json(*parts):
+    try:
+        return json.load(open(os.path.join(ROOT, *parts)))
+    except (OSError, ValueError):
+        return None
+
+
+# oracle work kinds charged to each GPU kernel kind
+ORACLE_KIND = {"k_gemm": ("gemm",), "k_qr": ("qr",), "k_qapply": (), "k_svd": ("svd",), "k_norm": ("norm",)}
+
+
+def method_work(grid, eps):
+    """Oracle-counted work of one product of the workload (None if not recorded)."""
+    wc = load_json("tests", "golden", "work_counts.json")
+    if not wc:
+        return None
+    return wc["cases"].get(f"grid2d_n{grid * grid}_eps{eps:g}")
 
 
 def fp64_peak():
@@ -303,7 +330,12 @@ def main():
     prof_total = sum(p.ms for _, p in kinds)
     dom_name, dom = max(kinds, key=lambda kv: kv[1].ms)
     peak = fp64_peak()
-    achieved = dom.flops / (dom.ms / 1e3) / 1e12 if dom.ms > 0 else 0.0
+    executed = dom.flops / (dom.ms / 1e3) / 1e12 if dom.ms > 0 else 0.0
+    mw = method_work(grid, EPS)
+    method_flops = sum(mw["flops"][k] for k in ORACLE_KIND.get(dom_name, ())) if mw else None
+    achieved = method_flops / (dom.ms / 1e3) / 1e12 if (method_flops and dom.ms > 0) else executed
+    hbm_peak = (load_json("MEASURED_PEAKS.json") or {}).get("hbm_gbs")
+    kc = dict(kinds).get("k_copy")
     # DRAM bytes per launch from the committed ncu capture, valid only while the
     # kernel source is the one the counters were taken on
     traffic = None
@@ -340,9 +372,26 @@ def main():
             "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
                          "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                         "launches": dom.launches, "flop_per_launch": dom.flops / dom.launches if dom.launches else None,
+                         "launches": dom.launches,
+                         "flop_per_launch": (method_flops if method_flops else dom.flops) / dom.launches
+                         if dom.launches else None,
+                         "work_source": "oracle counters, tests/golden/work_counts.json" if method_flops
+                         else "kernel counts (no oracle count recorded for this workload)",
                          "peak_source": "FP64 ALU peak derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
-                         "share": dom.ms / prof_total if prof_total else None},
+                         "share": dom.ms / prof_total if prof_total else None,
+                         "executed": {"achieved": executed, "frac": executed / peak if peak else None,
+                                      "gpu_flops_per_product": dom.flops,
+                                      "method_flops_per_product": method_flops,
+                                      "gpu_over_method": dom.flops / method_flops if method_flops else None},
+                         "product": {"method_gflop": sum(mw["flops"].values()) / 1e9 if mw else None,
+                                     "gpu_gflop": sum(p.flops for _, p in kinds) / 1e9,
+                                     "method_tflops_over_product_time":
+                                         sum(mw["flops"].values()) / (prof_total / 1e3) / 1e12 if mw else None},
+                         "hbm_copy": {"kernel": "k_copy", "gb": kc.bytes / 1e9, "ms": kc.ms,
+                                      "achieved_gbs": kc.bytes / (kc.ms / 1e3) / 1e9 if kc.ms > 0 else None,
+                                      "peak_gbs": hbm_peak,
+                                      "frac": (kc.bytes / (kc.ms / 1e3) / 1e9) / hbm_peak
+                                      if (kc.ms > 0 and hbm_peak) else None} if kc else None},
             "kernels": {nm: {"launches": p.launches, "jobs": p.jobs, "ms": round(p.ms, 4),
                              "gflop": round(p.flops / 1e9, 4), "gb": round(p.bytes / 1e9, 4)} for nm, p in kinds},
             "product": {"nadm": st0.nadm, "ninadm": st0.ninadm, "agglomerated": st0.nagglomerated,

@@ -87,13 +87,17 @@ typedef struct {
  *                  decisions and norms stay FP64.  Other values: H2_EINVAL.
  *   sync       1 = return after the product is complete and report device errors;
  *              0 = return after enqueueing (errors are reported by h2_check)
- *   stream     cudaStream_t to run on, or NULL for the library stream */
+ *   stream     cudaStream_t to run on, or NULL for the library stream
+ *   svd_max_sweeps  sweep cap of every Jacobi SVD of the product; 0 selects 60.
+ *              A job that reaches the cap still completes (its singular values
+ *              are those of the last sweep) and the product reports H2_ENOCONV. */
 typedef struct {
   double theta;
   int max_rank;
   int precision;
   int sync;
   void* stream;
+  int svd_max_sweeps;
 } h2_mul_opts;
 
 typedef struct {
@@ -150,7 +154,12 @@ int h2_mul_profile(const h2_matrix* A, const h2_matrix* B, double eps, const h2_
 /* Device error state of a product computed with sync = 0 (waits for it). */
 int h2_check(const h2_matrix* C);
 
-/* y = A x.  x, y of length n (caller ordering); on_device = 1: both are device
+/* y = A x by the H^2 matrix-vector product of Section 2 (complexity O(nk)
+ * stated there for Def. 4's representation): forward transform
+ * x^_s = W_s^* x|_s up the column tree through the transfer matrices,
+ * couplings y^_t += S_ts x^_s over the admissible leaves, backward transform
+ * down the row tree, leaf bases, and the dense nearfield blocks.
+ * x, y of length n (caller ordering); on_device = 1: both are device
  * pointers, else host pointers.  Runs on the library stream and synchronizes. */
 int h2_matvec(const h2_matrix* A, const double* x, double* y, int on_device);
 
@@ -231,21 +240,26 @@ int h2_ranks(const h2_matrix* A, int* row_ranks, int* col_ranks);
 /* Cluster-order permutation: perm[i] = original index of the i-th point. */
 int h2_permutation(const h2_matrix* A, int64_t* perm);
 
-/* y = A x without any allocation, for callers that cannot call cudaMalloc
- * (work enqueued inside a CUDA stream capture, where allocation is not a
- * capturable operation; latency-critical loops that must stay out of the
- * allocator; devices whose memory is partitioned up front).  The paper has no
- * counterpart: this is a convenience of the library.
+/* y = A x without any allocation, for callers that cannot call cudaMalloc:
+ * latency-critical loops that must stay out of the allocator (an allocation
+ * can synchronise the device), and processes whose device memory is
+ * partitioned up front (owned by another allocator, or a fixed budget with no
+ * room left).  The paper has no counterpart: this is a convenience of the
+ * library.
  *   x, y    DEVICE vectors of length n in the library's CLUSTER ordering
- *           (h2_permutation maps it to the caller's ordering); y is overwritten
- *   stream  cudaStream_t to enqueue on (NULL: legacy default stream); the call
- *           returns without waiting for the GPU
+ *           (h2_permutation maps it to the caller's ordering) on the current
+ *           device, like A's storage (else H2_EINVAL); y is overwritten
+ *   stream  cudaStream_t to enqueue on (NULL: legacy default stream).  The
+ *           call returns without waiting for the GPU; when A is a product
+ *           still being computed, the stream waits for it on the device.
  * Scratch: one static device array of 2^20 doubles (8 MiB) in every process and
  * on every GPU that loads the library, held until exit.  A call needs
  * 2 * nclusters * kpad doubles of it and returns H2_ENOMEM beyond that.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
- * share the array: calls that overlap on the GPU race; serialise them. */
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array, which keeps the last call's contents (each call
+ * clears what must start at zero): calls that overlap on the GPU race, so
+ * serialise them (host threads are serialised by the call itself). */
 int h2_matvec_noalloc(const h2_matrix* A, const double* x, double* y, void* stream);
 
 void h2_free(h2_matrix* A);

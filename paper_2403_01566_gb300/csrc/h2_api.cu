@@ -747,7 +747,7 @@ struct MulArgs {
   h2_matrix* A = nullptr;
   h2_matrix* B = nullptr;
   double eps = 0, theta = 0.25;
-  int max_rank = 0, precision = 0;
+  int max_rank = 0, precision = 0, svd_sweeps = 0;
   bool sync = true;
   cudaStream_t stream = nullptr;
   PlanKey key{};
@@ -767,6 +767,8 @@ static int mul_args(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   if (m.precision < 0 || m.precision > 2) return H2_EINVAL;
   if (m.max_rank < 0 || m.max_rank > GEMM_MAXTILE) return H2_EINVAL;
   m.sync = opts ? opts->sync != 0 : true;
+  m.svd_sweeps = opts ? opts->svd_max_sweeps : 0;
+  if (m.svd_sweeps < 0) return H2_EINVAL;
   m.stream = (opts && opts->stream) ? (cudaStream_t)opts->stream : g_stream;
   m.key = PlanKey{matrix_sig(m.A), matrix_sig(m.B),
                   (m.precision * 100 + m.max_rank) * 1000 + (int)std::lround(m.theta * 997.0)};
@@ -847,7 +849,7 @@ static int enqueue_product(const MulArgs& m, PlanRT& rt, cudaStream_t s, h2_kern
   }
   cudaMemsetAsync(C->d_arena, 0, P.c_len * sizeof(double), s);
   const double params[PARAM_COUNT] = {m.eps / 4.0 * std::sqrt(1.0 - 2.0 * m.theta), m.eps / 3.0,
-                                       svd_noise_floor(m.eps, m.precision)};
+                                       svd_noise_floor(m.eps, m.precision), (double)m.svd_sweeps};
   rc = prof ? run_plan_profiled(rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, prof)
             : run_plan(rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, true);
   if (rc) {

@@ -1060,8 +1060,9 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
   // dot products: thread -> (pair, row segment)
   const int nseg = blockDim.x / npairs;
   const int ap = threadIdx.x % npairs, aseg = threadIdx.x / npairs;
+  const int maxsweep = x.scal[PARAM_SVD_SWEEPS] >= 1.0 ? (int)x.scal[PARAM_SVD_SWEEPS] : SVD_MAXSWEEP;
   int sweep = 0;
-  for (; sweep < SVD_MAXSWEEP; ++sweep) {
+  for (; sweep < maxsweep; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int rnd = 0; rnd < ce - 1; ++rnd) {
@@ -1141,7 +1142,7 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
     col_norms();
   }
   if (threadIdx.x == 0) {
-    if (sweep >= SVD_MAXSWEEP) set_err(x, -5);
+    if (sweep >= maxsweep) set_err(x, -5);
     if (x.svd_sweeps) {
       x.svd_sweeps[2 * (first + blockIdx.x)] = sweep + 1;
       x.svd_sweeps[2 * (first + blockIdx.x) + 1] = nrot;

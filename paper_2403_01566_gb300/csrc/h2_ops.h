@@ -171,7 +171,9 @@ struct Stage {
 // PARAM_SVD_FLOOR: squared relative noise floor of the Jacobi SVD (columns
 // with ||m||^2 below it times ||M||_F^2 count as rounding noise: sigma = 0,
 // never rotated); set per product from eps and the contraction precision.
-enum ParamIdx : int { PARAM_TOL_BASIS = 0, PARAM_TOL_AGG = 1, PARAM_SVD_FLOOR = 2, PARAM_COUNT = 3 };
+// PARAM_SVD_SWEEPS: sweep cap of the Jacobi SVDs (values < 1: the default of
+// 60); a job that reaches it sets the error flag -5 (H2_ENOCONV).
+enum ParamIdx : int { PARAM_TOL_BASIS = 0, PARAM_TOL_AGG = 1, PARAM_SVD_FLOOR = 2, PARAM_SVD_SWEEPS = 3, PARAM_COUNT = 4 };
 
 // Kernel parameters common to all stages.
 // It lives in device memory (one control block per plan) so that a captured

@@ -26,7 +26,7 @@ class BuildOpts(C.Structure):
 
 class MulOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("max_rank", C.c_int), ("precision", C.c_int), ("sync", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("svd_max_sweeps", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -192,11 +192,13 @@ def build(points, kernel, eta, leaf_size, order) -> H2Matrix:
 
 
 def mul(A: H2Matrix, B: H2Matrix, eps: float, max_rank: int = 0, theta: float = 0.0, sync: bool = True,
-        stream=None, precision: int = 0) -> H2Matrix:
-    """C ~ A*B with block-relative error eps (h2_mul); precision 1 = FP32 contractions."""
+        stream=None, precision: int = 0, svd_max_sweeps: int = 0) -> H2Matrix:
+    """C ~ A*B with block-relative error eps (h2_mul); precision selects the
+    contraction arithmetic (h2_mul_opts.precision)."""
     o = MulOpts()
     o.theta, o.max_rank, o.precision, o.sync = float(theta), int(max_rank), int(precision), 1 if sync else 0
     o.stream = stream
+    o.svd_max_sweeps = int(svd_max_sweeps)
     h = C.c_void_p()
     _check(_lib().h2_mul(A.handle, B.handle, float(eps), C.byref(o), C.byref(h)), "h2_mul")
     return H2Matrix(h.value)

@@ -9,7 +9,7 @@
 // spectral norms (as the largest singular value) and rank prefix sums.
 //
 // Usage: stage_interpreter points.bin n dim leaf order eta eps
-//            kindA sA dA wA kindB sB dB wB max_rank hmatrix out.bin
+//            kindA sA dA wA kindB sB dB wB max_rank hmatrix out.bin [svd_sweeps]
 // out.bin: dense n x n product (row-major, caller ordering), then the row and
 // column ranks per cluster (int32, level order); with hmatrix = 1 the
 // H-matrix output variant is expanded instead and no ranks are written.
@@ -20,10 +20,12 @@
 #include <cstring>
 #include <vector>
 
-#include "../../paper_2403_01566_gb300/csrc/h2_build.h"
+#include "host_assembly.h"
 #include "../../paper_2403_01566_gb300/csrc/h2_plan.h"
 
 using namespace h2;
+using h2host::HostH2;
+using h2host::assemble_chebyshev;
 
 namespace {
 
@@ -238,7 +240,8 @@ struct Interp {
     for (double v : M) fro += v * v;
     const double tiny2 = fro * scal[PARAM_SVD_FLOOR];
     bool converged = false;
-    for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
+    const int maxsweep = scal[PARAM_SVD_SWEEPS] >= 1.0 ? (int)scal[PARAM_SVD_SWEEPS] : 60;
+    for (int sweep = 0; sweep < maxsweep && !converged; ++sweep) {
       converged = true;
       for (int i = 0; i < cols; ++i)
         for (int j = i + 1; j < cols; ++j) {
@@ -262,7 +265,7 @@ struct Interp {
           }
           converged = false;
         }
-      if (!converged && sweep == 59) err = -5;
+      if (!converged && sweep == maxsweep - 1) err = -5;
     }
     std::vector<double> sn(cols);
     std::vector<int> pos(cols);
@@ -365,7 +368,7 @@ std::vector<double> level_bases(const Tree& T, int k, const double* V, const dou
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc != 19) {
+  if (argc != 19 && argc != 20) {
     std::fprintf(stderr, "usage: see the header of stage_interpreter.cpp\n");
     return 2;
   }
@@ -442,6 +445,7 @@ int main(int argc, char** argv) {
   const double fl = eps > 0.0 ? std::min(std::ldexp(1.0, -40), std::max(std::ldexp(1.0, -50), eps * std::ldexp(1.0, -20)))
                               : std::ldexp(1.0, -50);
   E.scal[PARAM_SVD_FLOOR] = fl * fl;
+  E.scal[PARAM_SVD_SWEEPS] = argc > 19 ? std::atof(argv[19]) : 0.0;
   E.run(*P);
   if (E.err != 0) {
     std::fprintf(stderr, "interpreter error %d\n", E.err);

@@ -29,6 +29,8 @@ def test_strerror_codes(lib):
     for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert lib.h2_strerror(code)
     assert lib.h2_strerror(-7).decode().startswith("adaptive rank")
+    assert "did not converge" in lib.h2_strerror(h2.H2_ENOCONV).decode()
+    assert "timed out" in lib.h2_strerror(h2.H2_ETIMEOUT).decode()
 
 
 def test_build_rejects_invalid_arguments(lib):

@@ -30,6 +30,7 @@ def interpreter(tmp_path_factory):
     exe = str(tmp_path_factory.mktemp("interp") / "stage_interpreter")
     cmd = [gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-o", exe,
            os.path.join(ROOT, "tests", "host", "stage_interpreter.cpp"),
+           os.path.join(ROOT, "tests", "host", "host_assembly.cpp"),
            os.path.join(CSRC, "h2_plan.cpp"), os.path.join(CSRC, "h2_build.cpp"),
            "-I", os.path.join(ROOT, "include"), "-I", cuda_inc]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -37,7 +38,7 @@ def interpreter(tmp_path_factory):
     return exe
 
 
-def run_interpreter(exe, w, eps, tmp_path, hmatrix=False, max_rank=0):
+def run_interpreter(exe, w, eps, tmp_path, hmatrix=False, max_rank=0, svd_sweeps=None, expect_rc=0):
     pts = tmp_path / "pts.bin"
     out = tmp_path / "out.bin"
     np.ascontiguousarray(w.points, dtype=np.float64).tofile(pts)
@@ -46,7 +47,12 @@ def run_interpreter(exe, w, eps, tmp_path, hmatrix=False, max_rank=0):
             str(ka.kind), repr(ka.scale), repr(ka.diag), repr(ka.width),
             str(kb.kind), repr(kb.scale), repr(kb.diag), repr(kb.width), str(max_rank), "1" if hmatrix else "0",
             str(out)]
+    if svd_sweeps is not None:
+        args.append(str(svd_sweeps))
     r = subprocess.run(args, capture_output=True, text=True, timeout=600)
+    if expect_rc != 0:
+        assert r.returncode == expect_rc, r.stderr[-2000:]
+        return r.stderr
     assert r.returncode == 0, r.stderr[-2000:]
     raw = np.fromfile(out, dtype=np.uint8)
     n = w.n
@@ -109,3 +115,14 @@ def test_planned_hmatrix_variant_reproduces_the_oracle_factors(interpreter, tmp_
             Do[np.ix_(b.t.idx, b.s.idx)] = L @ R.T
     Z = X.dense() @ Y.dense()
     assert worst_blockrel(D, Do, Z, res.C.blocks) <= 1e-10
+
+
+def test_svd_sweep_cap_reports_nonconvergence(interpreter, tmp_path):
+    """The sweep cap of the Jacobi SVDs is a per-product parameter: one sweep
+    cannot diagonalise the wide agglomeration merges, so the stage semantics
+    report the non-convergence code -5 (H2_ENOCONV at the C ABI) instead of
+    iterating on; with the default cap the same product converges."""
+    w = I.grid_2d(32)
+    err = run_interpreter(interpreter, w, 1e-6, tmp_path, svd_sweeps=1, expect_rc=4)
+    assert "interpreter error -5" in err
+    run_interpreter(interpreter, w, 1e-6, tmp_path, svd_sweeps=0)
