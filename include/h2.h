@@ -84,7 +84,18 @@ typedef struct {
  *              2 = compensated FP32 contractions in every GEMM stage: operands
  *                  split into FP32 hi + lo parts, error-free products and
  *                  compensated sums (about 1e-13 relative); QR, SVD, rank
- *                  decisions and norms stay FP64.  Other values: H2_EINVAL.
+ *                  decisions and norms stay FP64.
+ *              3 = every GEMM stage on the tensor cores (mma BF16 operands,
+ *                  FP32 accumulation) with 5 slices of 8 bits per operand
+ *                  (row and column scaled per k chunk of 32; exact FP32 sums
+ *                  of the slice products; compensated accumulation): 40 bits
+ *                  relative to the chunk's row and column maxima.
+ *              4 = the GEMM stages of 64 x 64 tiles on the tensor cores with
+ *                  7 slices (56 bits: about FP64 accuracy), the smaller ones
+ *                  as compensated FP32 (form 2); QR, SVD, rank decisions and
+ *                  norms FP64 in forms 1-4.
+ *              Forms 2-4 need the scaled operands within FP32's exponent
+ *              range (about 1e-30 to 1e30).  Other values: H2_EINVAL.
  *   sync       1 = return after the product is complete and report device errors;
  *              0 = return after enqueueing (errors are reported by h2_check)
  *   stream     cudaStream_t to run on, or NULL for the library stream

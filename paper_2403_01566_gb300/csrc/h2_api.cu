@@ -733,10 +733,13 @@ static int hmul_impl(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const
 // least 2^20 below the tightest relative truncation tolerance of the product
 // (eps/3/(2n^2) with n <= 8 in the agglomeration, and the basis tolerances);
 // eps = 0 keeps every direction above 2^-50.  Compensated contractions
-// (~1e-13 rounding): 2^-40.
+// (precision 2) and the 7-slice tensor-core form (precision 4), whose
+// rounding is about 1e-13 or below: 2^-40.  The 5-slice form (precision 3,
+// 40-bit slicing): 2^-30.
 static double svd_noise_floor(double eps, int precision) {
   double f;
-  if (precision == 2) f = 9.094947017729282e-13;  // 2^-40
+  if (precision == 2 || precision == 4) f = 9.094947017729282e-13;  // 2^-40
+  else if (precision == 3) f = 9.313225746154785e-10;                // 2^-30
   else if (eps > 0.0) f = std::min(9.094947017729282e-13, std::max(8.881784197001252e-16, eps * 9.5367431640625e-07));
   else f = 8.881784197001252e-16;  // 2^-50
   return f * f;
@@ -764,7 +767,7 @@ static int mul_args(const h2_matrix* Ac, const h2_matrix* Bc, double eps, const 
   if (!(m.theta < 0.5)) return H2_EINVAL;
   m.max_rank = opts ? opts->max_rank : 0;
   m.precision = opts ? opts->precision : 0;
-  if (m.precision < 0 || m.precision > 2) return H2_EINVAL;
+  if (m.precision < 0 || m.precision > 4) return H2_EINVAL;
   if (m.max_rank < 0 || m.max_rank > GEMM_MAXTILE) return H2_EINVAL;
   m.sync = opts ? opts->sync != 0 : true;
   m.svd_sweeps = opts ? opts->svd_max_sweeps : 0;

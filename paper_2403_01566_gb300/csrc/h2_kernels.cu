@@ -2,6 +2,9 @@
 // planner (see h2_ops.h):
 //   k_gemm    grouped small GEMM chains with index gathers (out = sum A B [C]),
 //             in FP64, FP32 or compensated FP32 (the precision forms)
+//   k_gemm_tc the same chains on the tensor cores (mma.sync BF16, FP32
+//             accumulation) with 8-bit operand slices: about FP64 accuracy
+//             with 7 slices, 40 bits with 5
 //   k_copy    strided copies / transposes / scalings with zero padding
 //   k_qr      Householder QR (the thin QR factorizations of Sections 5.1-5.2),
 //             column-pivoted where an SVD follows, optionally stopped at a
@@ -14,6 +17,7 @@
 // compensated forms is FP64 arithmetic.
 #include <cuda_runtime.h>
 #include <climits>
+#include <cstdint>
 #include <math.h>
 #include <stdint.h>
 
@@ -361,6 +365,401 @@ __global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const
       const double v = P::result(acc[q]);
       *p = O.beta ? (*p + v) : v;
     }
+}
+
+// ------------------------------------------------- tensor-core GEMM (BF16) ----
+// Contractions on the tensor cores (mma.sync m16n8k16: BF16 operands, FP32
+// accumulation) by operand slicing in the manner of Ozaki, Ogita, Oishi and
+// Rump ("Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer. Algorithms
+// 59, 2012), with S slices of 8 bits per operand.  The scheme, per k chunk of
+// TK = 32:
+//   * row i of op(A) gets the exponent e_i with 2^(e_i) > max_k |a_ik|, column
+//     j of op(B) the exponent f_j;
+//   * a_ik = 2^(e_i) sum_{p=1..S} al_ik^(p) 2^(-8p) + r_ik with integers
+//     |al^(p)| <= 255 (the bits of |a_ik| 2^(-e_i), 8 at a time, truncated:
+//     |r_ik| < 2^(e_i - 8S)), exact in BF16; b_kj likewise with be^(q);
+//   * the diagonal sums D_d = sum_{p+q=d} sum_{k in chunk} al^(p) be^(q),
+//     d = 2..S+1, have at most S (p, q) pairs of TK integer products below
+//     2^16: |D_d| <= S * 32 * 255^2 < 2^24, so the FP32 accumulation of the
+//     tensor cores adds them without rounding;
+//   * sum_k a_ik b_kj = 2^(e_i + f_j) sum_d 2^(-8d) D_d up to the dropped
+//     products (p + q > S + 1) and the remainders: about (S + 3) 2^(-8S) TK
+//     relative to max_k |a_ik| max_k |b_kj|.
+// The D_d of a chunk are added to a compensated FP32 pair (TwoSum for d <= 4,
+// plain FP32 sums of the smaller rest into the low word).  S = 7 (56 bits,
+// 28 products per 16 x 8 x 16 step) reaches about FP64 accuracy (precision
+// form 4); S = 5 (40 bits, 15 products) is the reduced form (precision 3).
+// The accuracy is relative to the row and column maxima of each chunk: a row
+// whose entries span 2^x in magnitude keeps 8S - x bits for its smallest ones.
+// Elements below 2^-1022 count as zero; like the compensated FP32 form, the
+// scaled partial sums must stay within FP32's exponent range.
+constexpr int TK = 32;        // k chunk
+constexpr int TKP = TK + 8;   // row length of a slice tile (BF16): conflict-free fragment loads
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// BF16 bits of the integer sg * v, 0 <= v <= 255 (exact: at most 8
+// significant bits); v + 2^23 is an FP32 whose low bits hold v.
+__device__ __forceinline__ uint32_t bf16_of_small(uint32_t v, uint32_t sg) {
+  const float f = __uint_as_float(0x4B000000u | v) - 8388608.0f;
+  return (__float_as_uint(f) >> 16) | sg;
+}
+
+// 2^E as FP32: 0 below the subnormal range, and 2^127 for E > 127 (outside
+// the supported range of these forms; finite, so that a zero sum stays zero)
+__device__ __forceinline__ float pow2f(int E) {
+  if (E >= -126) return __uint_as_float((uint32_t)(min(E, 127) + 127) << 23);
+  return E >= -149 ? __uint_as_float(1u << (E + 149)) : 0.0f;
+}
+
+// Fixed-point magnitude floor(|v| 2^(8S - e)) of an FP64 value v with
+// biased exponent Ev, e = Emax - 1022 (Emax the largest biased exponent of
+// its row or column): shift = 8S - 53 - (Emax - Ev).
+template <int S>
+__device__ __forceinline__ unsigned long long fixed_of_double(unsigned long long u, int Emax) {
+  const int Ev = (int)((u >> 52) & 0x7ff);
+  if (Ev == 0) return 0ull;
+  const unsigned long long mant = (u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  const int sh = 8 * S - 53 - (Emax - Ev);
+  if (sh >= 0) return mant << sh;
+  return -sh >= 64 ? 0ull : (mant >> -sh);
+}
+
+// Same for an FP32 value (a word of a compensated pair), its biased exponent
+// mapped to the FP64 bias: shift = 8S - 24 - (Emax - Ev).
+template <int S>
+__device__ __forceinline__ unsigned long long fixed_of_float(uint32_t u, int Emax) {
+  const int Ef = (int)((u >> 23) & 0xff);
+  if (Ef == 0) return 0ull;
+  const int Ev = Ef - 127 + 1023;
+  const unsigned long long mant = (unsigned long long)((u & 0x7FFFFFu) | 0x800000u);
+  const int sh = 8 * S - 24 - (Emax - Ev);
+  if (sh >= 0) return sh >= 64 ? 0ull : (mant << sh);
+  return -sh >= 64 ? 0ull : (mant >> -sh);
+}
+
+// Operand element as raw bits: an FP64 value, or a compensated pair (s, c)
+// renormalised so that |c| <= ulp(s) / 2 (s in the high word).
+struct TcRaw {
+  unsigned long long u;
+};
+
+__device__ __forceinline__ TcRaw raw_of_double(double v) { return TcRaw{(unsigned long long)__double_as_longlong(v)}; }
+__device__ __forceinline__ TcRaw raw_of_pair(float2 p) {
+  // TwoSum: h + l = s + c exactly, l within half an ulp of h
+  const float h = __fadd_rn(p.x, p.y);
+  const float z = __fsub_rn(h, p.x);
+  const float l = __fadd_rn(__fsub_rn(p.x, __fsub_rn(h, z)), __fsub_rn(p.y, z));
+  return TcRaw{((unsigned long long)__float_as_uint(h) << 32) | __float_as_uint(l)};
+}
+
+// Biased FP64-scale exponent of an element (0 for zero): the value's own, or
+// that of the pair's leading word.
+template <bool PAIR>
+__device__ __forceinline__ int raw_exp(TcRaw r) {
+  if (!PAIR) return (int)((r.u >> 52) & 0x7ff);
+  const int Ef = (int)((r.u >> 55) & 0xff);
+  return Ef == 0 ? 0 : Ef - 127 + 1023;
+}
+
+// Writes the S slices of an element, scaled by its row or column exponent
+// Emax, to dst[p * pstride] (BF16 bits).
+template <int S, bool PAIR>
+__device__ __forceinline__ void put_raw_slices(uint16_t* dst, int pstride, TcRaw r, int Emax) {
+  unsigned long long a;
+  bool neg;
+  if (!PAIR) {
+    a = fixed_of_double<S>(r.u, Emax);
+    neg = (r.u >> 63) != 0ull;
+  } else {
+    const uint32_t us = (uint32_t)(r.u >> 32), uc = (uint32_t)r.u;
+    long long f = (long long)fixed_of_float<S>(us, Emax);
+    if (us >> 31) f = -f;
+    const long long fc = (long long)fixed_of_float<S>(uc, Emax);
+    f += (uc >> 31) ? -fc : fc;
+    neg = f < 0;
+    a = (unsigned long long)(neg ? -f : f);
+  }
+  const uint32_t sg = neg ? 0x8000u : 0u;
+#pragma unroll
+  for (int p = 1; p <= S; ++p) {
+    const uint32_t v = (uint32_t)(a >> (8 * (S - p))) & 0xffu;
+    dst[(p - 1) * pstride] = (uint16_t)bf16_of_small(v, sg);
+  }
+}
+
+// Operand source of a chunk: global FP64 op(X) or the compensated pairs of a
+// three-factor intermediate in shared memory (row-major, ld; never transposed).
+struct TcSrc {
+  const double* g;  // global matrix (nullptr: use s)
+  const float2* s;  // shared pairs
+  int ld, t;
+};
+
+constexpr int TC_NE = (64 * TK) / 256;  // elements of an operand chunk per thread at most
+
+// Stages the slices of a chunk of an operand: rows 0..R16 (R16 = rows rounded
+// up to 16 or 8) by k = k0..k0+TK, element (r, k) = X(r, k0 + k) where
+// X(r, k) = g[r * ld + k] (along = true: consecutive k consecutive in memory)
+// or g[k * ld + r] (along = false), or the shared pairs s[r * ld + k].
+// Slices go to dst[p][r][k] (row length TKP), the exponents to rexp[r].
+// along: a warp holds one row (lane = k), its maximum is a warp reduction;
+// otherwise the maxima meet in shared memory (zeroed by the caller) and a
+// second pass slices.
+template <int S, bool PAIR>
+__device__ __forceinline__ void tc_stage(uint16_t* dst, int R16, int* rexp, const TcSrc& X, bool along, int rows,
+                                         int k0, int kc) {
+  const int total = R16 * TK;
+  const int pstride = R16 * TKP;
+  if (along) {
+#pragma unroll 1
+    for (int it = 0; it < TC_NE; ++it) {
+      const int e = threadIdx.x + 256 * it;
+      if (e >= total) break;
+      const int r = e / TK, k = e % TK;
+      TcRaw v{0ull};
+      if (r < rows && k < kc) {
+        if (PAIR) v = raw_of_pair(X.s[r * X.ld + k0 + k]);
+        else v = raw_of_double(X.g[(int64_t)r * X.ld + k0 + k]);
+      }
+      const int Emax = __reduce_max_sync(0xffffffffu, raw_exp<PAIR>(v));
+      if ((threadIdx.x & 31) == 0) rexp[r] = Emax;
+      put_raw_slices<S, PAIR>(dst + r * TKP + k, pstride, v, Emax);
+    }
+    return;
+  }
+  // two passes over the elements (the second read hits L1).  A warp takes
+  // a block of 8 rows x 4 k: 64-byte runs of consecutive r in memory, and
+  // slice stores into 16 distinct banks (row length TKP = 20 words).
+  const int nrb = R16 >> 3;
+#pragma unroll 1
+  for (int it = 0; it < TC_NE; ++it) {
+    const int e = threadIdx.x + 256 * it;
+    if (e >= total) break;
+    const int b = e >> 5, ln = e & 31;
+    const int r = (b % nrb) * 8 + (ln & 7), k = (b / nrb) * 4 + (ln >> 3);
+    const int E = (r < rows && k < kc) ? raw_exp<false>(raw_of_double(X.g[(int64_t)(k0 + k) * X.ld + r])) : 0;
+    if (E) atomicMax(&rexp[r], E);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < TC_NE; ++it) {
+    const int e = threadIdx.x + 256 * it;
+    if (e >= total) break;
+    const int b = e >> 5, ln = e & 31;
+    const int r = (b % nrb) * 8 + (ln & 7), k = (b / nrb) * 4 + (ln >> 3);
+    const TcRaw v = (r < rows && k < kc) ? raw_of_double(X.g[(int64_t)(k0 + k) * X.ld + r]) : TcRaw{0ull};
+    put_raw_slices<S, false>(dst + r * TKP + k, pstride, v, rexp[r]);
+  }
+}
+
+// Adds the diagonal sums D (d = j + 2) of fragment element (r, c), scaled by
+// 2^(e_r + f_c - 8d) and alpha = ah + al, to the compensated pair (s, c):
+// TwoSum for d <= 4, the smaller rest summed in FP32 into the low word.
+template <int S>
+__device__ __forceinline__ void tc_flush(float& ss, float& cc, const float (&D)[S][4], int e, int E0, float ah,
+                                         float al) {
+  float sc = pow2f(E0 - 16);
+  float low = 0.0f;
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+    const float v = D[j][e] * sc;  // exact (a power-of-two scaling of an integer below 2^24)
+    sc *= 0.00390625f;             // 2^-8
+    if (j < 3) {
+      const float ph = __fmul_rn(ah, v);
+      const float pl = fmaf(al, v, fmaf(ah, v, -ph));  // ah v = ph + exact error, plus al v
+      const float t = __fadd_rn(ss, ph);
+      const float z = __fsub_rn(t, ss);
+      const float err = __fadd_rn(__fsub_rn(ss, __fsub_rn(t, z)), __fsub_rn(ph, z));
+      ss = t;
+      cc = __fadd_rn(cc, __fadd_rn(err, pl));
+    } else {
+      low = fmaf(ah, v, low);
+    }
+  }
+  cc = __fadd_rn(cc, low);
+}
+
+// Accumulates alpha op(A)(m x K) op(B)(K x n) into this warp's fragment
+// elements (tile = warp + 8 ti of the ceil(m/16) x ceil(n/8) tiles; element
+// e: row g + 8 (e >> 1), column 2 tq + (e & 1) of the tile): into acc, or,
+// with TOSMEM, into the compensated pairs ts[r * ldts + c] in shared memory.
+template <int S, int TPW, bool APAIR, bool TOSMEM>
+__device__ void tc_product(DF (&acc)[TPW][4], float2* ts, int ldts, const TcSrc& A, const double* B, int ldb,
+                           int tb, int m, int n, int K, double alpha, uint16_t* As, uint16_t* Bs, int* rexp,
+                           int* cexp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+  const int m16 = (m + 15) & ~15, n8 = (n + 7) & ~7;
+  const int nt = n8 >> 3, ntiles = (m16 >> 4) * nt;
+  const float2 al2 = split_df(alpha);
+  const bool a_along = APAIR || !A.t, b_along = tb != 0;
+  const TcSrc Bsrc{B, nullptr, ldb, tb};
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    const int kc = min(TK, K - k0);
+    __syncthreads();  // the previous chunk's slices and exponents are consumed
+    if (!a_along || !b_along) {
+      for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        if (!a_along) rexp[i] = 0;
+        if (!b_along) cexp[i] = 0;
+      }
+      __syncthreads();
+    }
+    tc_stage<S, APAIR>(As, m16, rexp, A, a_along, m, k0, kc);
+    tc_stage<S, false>(Bs, n8, cexp, Bsrc, b_along, n, k0, kc);
+    __syncthreads();
+    const int ksteps = (kc + 15) >> 4;
+#pragma unroll
+    for (int ti = 0; ti < TPW; ++ti) {
+      const int tile = warp + 8 * ti;
+      if (tile >= ntiles) break;
+      const int tr = (tile / nt) * 16, tcn = (tile % nt) * 8;
+      float D[S][4];
+#pragma unroll
+      for (int d = 0; d < S; ++d) D[d][0] = D[d][1] = D[d][2] = D[d][3] = 0.0f;
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const int kb = ks * 16 + 2 * tq;
+        uint32_t b0[S], b1[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          const uint16_t* bp = Bs + q * n8 * TKP + (tcn + g) * TKP + kb;
+          b0[q] = *reinterpret_cast<const uint32_t*>(bp);
+          b1[q] = *reinterpret_cast<const uint32_t*>(bp + 8);
+        }
+#pragma unroll
+        for (int p = 0; p < S; ++p) {
+          const uint16_t* ap = As + p * m16 * TKP + (tr + g) * TKP + kb;
+          const uint32_t a0 = *reinterpret_cast<const uint32_t*>(ap);
+          const uint32_t a1 = *reinterpret_cast<const uint32_t*>(ap + 8 * TKP);
+          const uint32_t a2 = *reinterpret_cast<const uint32_t*>(ap + 8);
+          const uint32_t a3 = *reinterpret_cast<const uint32_t*>(ap + 8 * TKP + 8);
+#pragma unroll
+          for (int q = 0; q < S - p; ++q) mma_bf16(D[p + q], a0, a1, a2, a3, b0[q], b1[q]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = tr + g + 8 * (e >> 1), c = tcn + 2 * tq + (e & 1);
+        if (r >= m || c >= n) continue;
+        const int er = rexp[r], fc = cexp[c];
+        if (er == 0 || fc == 0) continue;
+        const int E0 = (er - 1022) + (fc - 1022);
+        if (TOSMEM) {
+          float2 v = ts[r * ldts + c];
+          tc_flush<S>(v.x, v.y, D, e, E0, al2.x, al2.y);
+          ts[r * ldts + c] = v;
+        } else {
+          tc_flush<S>(acc[ti][e].s, acc[ti][e].c, D, e, E0, al2.x, al2.y);
+        }
+      }
+    }
+  }
+}
+
+// One CTA per output tile (<= 64 x 64) of a GemmOut with its terms, as k_gemm,
+// with every contraction on the tensor cores.  S slices (see above); TPW =
+// tiles per warp of the stage's largest tile (1, 2 or 4).  A three-factor
+// term alpha op(A) op(B) op(C) forms Ts = op(A) op(B) as compensated pairs in
+// shared memory (when the stage has such terms: shared memory for them is
+// part of the launch), then adds alpha Ts op(C).
+template <int S, int TPW>
+__global__ void __launch_bounds__(256, 2)
+    k_gemm_tc(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs, const GemmTerm* __restrict__ terms,
+              int mmax, int nb) {
+  const ExecCtx& x = *px;
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  const int m16max = (mmax + 15) & ~15, n8max = (nb + 7) & ~7;
+  uint16_t* As = reinterpret_cast<uint16_t*>(tc_raw);
+  uint16_t* Bs = As + S * m16max * TKP;
+  int* rexp = reinterpret_cast<int*>(Bs + S * n8max * TKP);
+  int* cexp = rexp + 64;
+  float2* Ts = reinterpret_cast<float2*>(cexp + 64);
+  const int ldts = nb + 1;
+  const GemmOut& O = outs[blockIdx.x];
+  const int m = dimv(O.m, x.slot);
+  const int n = O.clampn ? min(dimv(O.n, x.slot), GT) : dimv(O.n, x.slot);
+  if (m <= 0 || n <= 0) return;
+  if (m > mmax || n > nb || ((m + 15) / 16) * ((n + 7) / 8) > 8 * TPW) {
+    if (threadIdx.x == 0) set_err(x, -9);
+    return;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+  const int nt = (n + 7) >> 3, ntiles = ((m + 15) >> 4) * nt;
+  DF acc[TPW][4];
+#pragma unroll
+  for (int ti = 0; ti < TPW; ++ti)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[ti][e] = DF{0.0f, 0.0f};
+
+  for (int tix = O.t0; tix < O.t1; ++tix) {
+    const GemmTerm& Tm = terms[tix];
+    double alpha = Tm.alpha;
+    if (Tm.scale_idx >= 0) alpha *= x.scal[Tm.scale_idx];
+    const double* A = ptrv(Tm.a, x);
+    const double* B = ptrv(Tm.b, x);
+    const double* C = ptrv(Tm.c, x);
+    if (B == nullptr) {  // plain add of op(A) (m x n)
+#pragma unroll
+      for (int ti = 0; ti < TPW; ++ti) {
+        const int tile = warp + 8 * ti;
+        if (tile >= ntiles) break;
+        const int tr = (tile / nt) * 16, tcn = (tile % nt) * 8;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = tr + g + 8 * (e >> 1), c = tcn + 2 * tq + (e & 1);
+          if (r < m && c < n) GemmPol<GM_DF>::oadd_plain(acc[ti][e], alpha, ld_op(A, Tm.lda, Tm.ta, r, c));
+        }
+      }
+      continue;
+    }
+    const int k1 = dimv(Tm.k1, x.slot);
+    if (C == nullptr) {
+      tc_product<S, TPW, false, false>(acc, nullptr, 0, TcSrc{A, nullptr, Tm.lda, Tm.ta}, B, Tm.ldb, Tm.tb, m, n,
+                                       k1, alpha, As, Bs, rexp, cexp);
+      continue;
+    }
+    // three-factor term: Ts = op(A) op(B) (m x nn), then alpha Ts op(C)
+    const int nn = dimv(Tm.k2, x.slot);
+    if (nn <= 0) continue;
+    if (nn > nb || ((m + 15) / 16) * ((nn + 7) / 8) > 8 * TPW) {
+      if (threadIdx.x == 0) set_err(x, -9);
+      return;
+    }
+    __syncthreads();  // an earlier term's reads of Ts are done
+    for (int e = threadIdx.x; e < m * ldts; e += blockDim.x) Ts[e] = make_float2(0.0f, 0.0f);
+    tc_product<S, TPW, false, true>(acc, Ts, ldts, TcSrc{A, nullptr, Tm.lda, Tm.ta}, B, Tm.ldb, Tm.tb, m, nn, k1,
+                                    1.0, As, Bs, rexp, cexp);
+    tc_product<S, TPW, true, false>(acc, nullptr, 0, TcSrc{nullptr, Ts, ldts, 0}, C, Tm.ldc, Tm.tc, m, n, nn, alpha,
+                                    As, Bs, rexp, cexp);
+  }
+  double* out = ptrv(O.o, x);
+#pragma unroll
+  for (int ti = 0; ti < TPW; ++ti) {
+    const int tile = warp + 8 * ti;
+    if (tile >= ntiles) break;
+    const int tr = (tile / nt) * 16, tcn = (tile % nt) * 8;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = tr + g + 8 * (e >> 1), c = tcn + 2 * tq + (e & 1);
+      if (r < m && c < n) {
+        double* p = out + (int64_t)r * O.ldo + c;
+        const double v = GemmPol<GM_DF>::result(acc[ti][e]);
+        *p = O.beta ? (*p + v) : v;
+      }
+    }
+  }
+}
+
+// Dynamic shared memory of a tensor-core GEMM stage (bytes).
+__host__ __device__ constexpr int gemm_tc_smem_bytes(int S, int mmax, int nb) {
+  return 2 * S * (((mmax + 15) & ~15) + ((nb + 7) & ~7)) * TKP + 2 * 64 * 4 + 8 * mmax * (nb + 1);
 }
 
 // ------------------------------------------------------------------ copy ----
@@ -1374,6 +1773,13 @@ cudaError_t kernels_init() {
   H2_GEMM_ATTR(1, GM_F32) H2_GEMM_ATTR(4, GM_F32) H2_GEMM_ATTR(GQ, GM_F32)
   H2_GEMM_ATTR(1, GM_DF) H2_GEMM_ATTR(4, GM_DF) H2_GEMM_ATTR(GQ, GM_DF)
 #undef H2_GEMM_ATTR
+#define H2_GEMM_TC_ATTR(S, T)                                                                      \
+  if (e == cudaSuccess)                                                                            \
+    e = cudaFuncSetAttribute(k_gemm_tc<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                             gemm_tc_smem_bytes(S, GT, GT));
+  H2_GEMM_TC_ATTR(5, 1) H2_GEMM_TC_ATTR(5, 2) H2_GEMM_TC_ATTR(5, 4)
+  H2_GEMM_TC_ATTR(7, 1) H2_GEMM_TC_ATTR(7, 2) H2_GEMM_TC_ATTR(7, 4)
+#undef H2_GEMM_TC_ATTR
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes(NORM_MAXN));
   if (e != cudaSuccess) return e;
@@ -1412,6 +1818,18 @@ static void launch_gemm(int mode, int qsteps, int count, size_t sm, cudaStream_t
     launch_gemm_mode<GM_F64>(qsteps, count, sm, s, x, go, gt, mmax, nb);
 }
 
+// tpw = tiles per warp of the stage's largest output tile
+template <int S>
+static void launch_gemm_tc(int tpw, int count, size_t sm, cudaStream_t s, const ExecCtx* x, const GemmOut* go,
+                           const GemmTerm* gt, int mmax, int nb) {
+  if (tpw <= 1)
+    k_gemm_tc<S, 1><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+  else if (tpw <= 2)
+    k_gemm_tc<S, 2><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+  else
+    k_gemm_tc<S, 4><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+}
+
 int stage_launches(const Stage& st) {
   return (st.kind == ST_SVD && st.smem > 8 * SVD_SMALL_DOUBLES) ? 2 : 1;
 }
@@ -1421,8 +1839,17 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaSt
   switch (st.kind) {
     case ST_GEMM:
     {
-      const int shape = st.aux & ~(GEMM_AUX_FP32 | GEMM_AUX_DF);
+      const int shape = st.aux & ~GEMM_AUX_FLAGS;
       const int mmax = shape ? ((shape >> 16) & 0xff) : GT, nb = shape ? (shape & 0xffff) : GT;
+      if (st.aux & (GEMM_AUX_TC5 | GEMM_AUX_TC7)) {
+        const int tiles = ((mmax + 15) / 16) * ((nb + 7) / 8), tpw = (tiles + 7) / 8;
+        const GemmOut* go = j.gemm_out + st.first;
+        if (st.aux & GEMM_AUX_TC7)
+          launch_gemm_tc<7>(tpw, st.count, gemm_tc_smem_bytes(7, mmax, nb), s, x, go, j.gemm_term, mmax, nb);
+        else
+          launch_gemm_tc<5>(tpw, st.count, gemm_tc_smem_bytes(5, mmax, nb), s, x, go, j.gemm_term, mmax, nb);
+        break;
+      }
       const int mode = (st.aux & GEMM_AUX_DF) ? GM_DF : (st.aux & GEMM_AUX_FP32) ? GM_F32 : GM_F64;
       const size_t sm = (mode == GM_F32 ? sizeof(float) : sizeof(double)) * gemm_smem_doubles(mmax, nb);
       const int rstep = 256 / nb;

@@ -10,6 +10,9 @@ constexpr int SVD_MAXDIM = 256;  // largest Jacobi SVD (rows and columns)
 constexpr int NORM_MAXN = 128;   // largest matrix of a spectral-norm job
 constexpr int GEMM_AUX_FP32 = 1 << 24;  // Stage::aux flag of a GEMM stage: FP32 products and sums
 constexpr int GEMM_AUX_DF = 1 << 25;    // Stage::aux flag of a GEMM stage: compensated FP32 (double-float)
+constexpr int GEMM_AUX_TC5 = 1 << 26;   // Stage::aux flag: tensor cores, 5 BF16 slices (40 bits)
+constexpr int GEMM_AUX_TC7 = 1 << 27;   // Stage::aux flag: tensor cores, 7 BF16 slices (about FP64)
+constexpr int GEMM_AUX_FLAGS = GEMM_AUX_FP32 | GEMM_AUX_DF | GEMM_AUX_TC5 | GEMM_AUX_TC7;
 // Dynamic shared memory of an SVD launch at most (the per-column arrays of a
 // job, then its matrix when that fits).  76 KB: two CTAs on an SM, which
 // leaves ~90 KB of L1 to the matrices that stay in global memory; a 72 KB cap

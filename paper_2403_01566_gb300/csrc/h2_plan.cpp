@@ -116,6 +116,8 @@ struct Builder {
   explicit Builder(Plan& p) : P(p) {}
   bool fp32_contractions = false;  // precision form 1
   bool df_contractions = false;    // precision form 2
+  bool tc5_contractions = false;   // precision form 3 (tensor cores, 5 slices)
+  bool tc7_contractions = false;   // precision form 4 (tensor cores, 7 slices, with compensated FP32)
   int64_t alloc(int64_t n) {
     const int64_t o = ws;
     ws += (std::max<int64_t>(n, 1) + 31) & ~int64_t(31);
@@ -173,8 +175,19 @@ struct Builder {
     // pushes, dense leaf products) and the coupling projection; agglomeration,
     // condensation and the bases stay FP64
     const bool f32 = fp32_contractions && (tag <= 9 || tag == 14);  // TAG_P .. TAG_DENSE, TAG_COUPLE
-    // compensated contractions (~1e-13): every GEMM stage
-    const int mode_flag = df_contractions ? GEMM_AUX_DF : f32 ? GEMM_AUX_FP32 : 0;
+    // Tensor cores for the stages whose static tile bound is 64 x 64 (the
+    // dense leaf products, merges, panels): there the slicing of an operand
+    // element is shared by 64 outputs.  On smaller tiles the slicing and the
+    // 15-28 slice products per step cost more than the compensated FP32
+    // arithmetic they replace (measured), so form 4 keeps those compensated.
+    const bool big = g_mmax >= 64 && g_nb >= 64;
+    // compensated contractions (~1e-13), the 7-slice tensor-core form (about
+    // FP64) and the 5-slice form: every GEMM stage
+    const int mode_flag = (tc7_contractions && big)  ? GEMM_AUX_TC7
+                          : (tc5_contractions)       ? GEMM_AUX_TC5
+                          : (df_contractions || tc7_contractions) ? GEMM_AUX_DF
+                          : f32                      ? GEMM_AUX_FP32
+                                                     : 0;
     P.stages.push_back(Stage{ST_GEMM, first, (int)go.size(), tag, 0, (g_mmax << 16) | g_nb | mode_flag});
     go.clear();
     gt.clear();
@@ -350,6 +363,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   Builder B(P);
   B.fp32_contractions = opt.precision == 1;
   B.df_contractions = opt.precision == 2;
+  B.tc5_contractions = opt.precision == 3;
+  B.tc7_contractions = opt.precision == 4;
   const Tree& TI = *X.rows;
   const Tree& TJ = *X.cols;
   const Tree& TK = *Y.cols;

@@ -30,7 +30,10 @@ struct MulOptions {
   double theta = 0.25;   // weight factor (Section 5.3)
   int max_rank = 0;      // cap of the adaptive ranks (storage padding of C)
   int precision = 0;     // 0 FP64 throughout; 1 FP32 contractions (accumulation and couplings);
-                         // 2 compensated FP32 contractions (all GEMM stages)
+                         // 2 compensated FP32 contractions (all GEMM stages);
+                         // 3 tensor-core 5-slice contractions (all GEMM stages);
+                         // 4 tensor-core 7-slice contractions on 64 x 64 stages,
+                         //   compensated FP32 on the others
   bool hmatrix = false;  // H-matrix output: stop after agglomeration (no nested-basis recompression)
 };
 

@@ -1,6 +1,10 @@
-"""The FP32-contraction form (h2_mul precision = 1) against the FP64 oracle.
+"""The reduced- and mixed-precision forms of h2_mul against the FP64 oracle.
 
-The accumulation phases and the coupling projection compute FP32 products with
+precision 1 (FP32 contractions), 2 (compensated FP32), 3 (tensor cores, 5
+BF16 slices) and 4 (tensor cores with 7 BF16 slices on the 64 x 64 stages,
+about FP64).
+
+Precision 1: the accumulation phases and the coupling projection compute FP32 products with
 FP32 sums; agglomeration, condensation, QR, SVD, rank decisions and norms stay
 FP64.  Requirements checked:
 
@@ -99,11 +103,66 @@ def test_compensated_contractions_match_oracle(w, eps):
     assert list(rc) == [res.ranks_col[c.id] for c in O.all_clusters(Y.cols)]
 
 
+@pytest.mark.parametrize("w,eps", CASES_DF, ids=[f"{w.name}-{e:g}" for w, e in CASES_DF])
+def test_tensor_core_slices_match_oracle(w, eps):
+    """precision 4: the 64 x 64 GEMM stages on the tensor cores with 7 BF16
+    slices per operand (exact FP32 diagonal sums, compensated accumulation),
+    the others compensated FP32, keep the FP64 result: within 1e-10 of the
+    oracle, within eps of the exact product, identical ranks; two runs are
+    bitwise equal."""
+    A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
+    B = h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order)
+    Ctc = h2.mul(A, B, eps, precision=4)
+    X, Y = build_pair(w)
+    res = O.multiply(X, Y, eps)
+    Z = X.dense() @ Y.dense()
+    Dtc = Ctc.to_dense()
+    d_oracle, d_exact = _blockrel(Dtc, res.C.dense(), Z, res.C.blocks)
+    print(f"\n{w.name} eps={eps:g}: tensor-core 7-slice form vs oracle {d_oracle:.3e}, vs exact {d_exact:.3e}")
+    assert d_oracle <= 1e-10, d_oracle
+    assert d_exact <= eps, d_exact
+    rr, rc = Ctc.ranks()
+    assert list(rr) == [res.ranks_row[c.id] for c in O.all_clusters(X.rows)]
+    assert list(rc) == [res.ranks_col[c.id] for c in O.all_clusters(Y.cols)]
+    assert np.array_equal(h2.mul(A, B, eps, precision=4).to_dense(), Dtc)
+
+
+CASES_TC5 = [
+    (I.plain_1d(1024), 1e-4),
+    (I.grid_2d(64), 1e-4),
+    (I.grid_2d(64), 1e-6),
+    (I.square_2d(1500, seed=7, leaf=32, order=3), 1e-4),
+    (I.cube_3d(2048, seed=13, leaf=64, order=4), 1e-4),
+]
+
+
+@pytest.mark.parametrize("w,eps", CASES_TC5, ids=[f"{w.name}-{e:g}" for w, e in CASES_TC5])
+def test_tensor_core_5slice_within_eps(w, eps):
+    """precision 3: every GEMM stage on the tensor cores with 5 BF16 slices
+    (40 bits relative to the chunk's row and column maxima); QR, SVD, rank
+    decisions and norms FP64.  Every admissible block stays within eps of the
+    exact product and of the FP64 oracle."""
+    A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
+    B = h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order)
+    Cb = h2.mul(A, B, eps, precision=3)
+    X, Y = build_pair(w)
+    res = O.multiply(X, Y, eps)
+    Z = X.dense() @ Y.dense()
+    d_oracle, d_exact = _blockrel(Cb.to_dense(), res.C.dense(), Z, res.C.blocks)
+    rr, rc = Cb.ranks()
+    ro = [res.ranks_row[c.id] for c in O.all_clusters(X.rows)]
+    print(f"\n{w.name} eps={eps:g}: tensor-core 5-slice form vs oracle {d_oracle:.3e}, vs exact {d_exact:.3e}; "
+          f"largest row rank {max(rr)} (oracle {max(ro)})")
+    assert d_exact <= eps, d_exact
+    assert d_oracle <= eps, d_oracle
+
+
 def test_precision_values():
     w = I.plain_1d(256)
     A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
-    with pytest.raises(h2.H2Error):
-        h2.mul(A, A, 1e-6, precision=3)
+    for bad in (-1, 5):
+        with pytest.raises(h2.H2Error):
+            h2.mul(A, A, 1e-6, precision=bad)
     # the FP64 and FP32 forms have separate cached plans
     C1 = h2.mul(A, A, 1e-6, precision=1)
     C0 = h2.mul(A, A, 1e-6, precision=0)
