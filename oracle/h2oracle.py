@@ -523,6 +523,140 @@ class H2:
         return y
 
 
+    # ---- restricted products, for checking blocks of a product at sizes
+    # where the product itself is out of the oracle's reach ----------------
+    def _leaves_by_col(self):
+        if not hasattr(self, "_bycol"):
+            self._bycol = {}
+            for b in block_leaves(self.blocks):
+                self._bycol.setdefault(b.s.id, []).append(b)
+        return self._bycol
+
+    def _leaves_by_row(self):
+        if not hasattr(self, "_byrow"):
+            self._byrow = {}
+            for b in block_leaves(self.blocks):
+                self._byrow.setdefault(b.t.id, []).append(b)
+        return self._byrow
+
+    def matmat_cluster(self, c, Xc):
+        """Y = G|_{I x c} Xc for a column cluster c and Xc (|c| x m), rows in
+        the row tree's cluster order: the matrix-vector product of Section 2
+        on columns supported in c.  The forward transform runs over c's
+        subtree and up its ancestors (the other clusters see zero), then the
+        couplings of the admissible leaves whose column cluster is among
+        them, the backward transform and the nearfield leaves inside c."""
+        m = Xc.shape[1]
+        xhat = {}
+
+        def fwd(s):
+            lo = s.off - c.off
+            if s.is_leaf:
+                xhat[s.id] = self.W.leaf[s.id].T @ Xc[lo:lo + s.size]
+            else:
+                acc = np.zeros((self.W.rank[s.id], m))
+                for ch in s.children:
+                    fwd(ch)
+                    acc += self.W.trans[ch.id].T @ xhat[ch.id]
+                xhat[s.id] = acc
+        fwd(c)
+        a = c
+        while a.parent is not None:
+            xhat[a.parent.id] = self.W.trans[a.id].T @ xhat[a.id]
+            a = a.parent
+        bycol = self._leaves_by_col()
+        yhat = {}
+        Y = np.zeros((self.rows.size, m))
+        for sid, xs in xhat.items():
+            for b in bycol.get(sid, []):
+                if b.adm:
+                    v = self.S[id(b)] @ xs
+                    yhat[b.t.id] = yhat[b.t.id] + v if b.t.id in yhat else v
+                else:
+                    lo = b.s.off - c.off
+                    Y[b.t.off:b.t.off + b.t.size] += self.N[id(b)] @ Xc[lo:lo + b.s.size]
+
+        def bwd(t, carry):
+            v = yhat.get(t.id)
+            if carry is not None:
+                v = carry if v is None else v + carry
+            if t.is_leaf:
+                if v is not None:
+                    Y[t.off:t.off + t.size] += self.V.leaf[t.id] @ v
+            else:
+                for ch in t.children:
+                    bwd(ch, None if v is None else self.V.trans[ch.id] @ v)
+        bwd(self.rows, None)
+        return Y
+
+    def rows_matmat(self, t, Z):
+        """(G Z)|_t for a row cluster t and Z (n_cols x m) in the column tree's
+        cluster order: the forward transform of Z over the whole column tree,
+        the couplings of the admissible leaves whose row cluster is t, one of
+        its ancestors or descendants, the backward transform restricted to t
+        and the nearfield leaves of rows inside t."""
+        m = Z.shape[1]
+        xhat = {}
+
+        def fwd(s):
+            if s.is_leaf:
+                xhat[s.id] = self.W.leaf[s.id].T @ Z[s.off:s.off + s.size]
+            else:
+                acc = np.zeros((self.W.rank[s.id], m))
+                for ch in s.children:
+                    fwd(ch)
+                    acc += self.W.trans[ch.id].T @ xhat[ch.id]
+                xhat[s.id] = acc
+        fwd(self.cols)
+        byrow = self._leaves_by_row()
+        out = np.zeros((t.size, m))
+        # couplings of t's ancestors, pushed down to t through the transfers
+        chain = []
+        a = t
+        while a is not None:
+            chain.append(a)
+            a = a.parent
+        carry = None
+        for a in reversed(chain):          # root first
+            if carry is not None and a is not chain[-1]:
+                carry = self.V.trans[a.id] @ carry
+            for b in byrow.get(a.id, []):
+                if b.adm:
+                    v = self.S[id(b)] @ xhat[b.s.id]
+                    carry = v if carry is None else carry + v
+                elif a is t:
+                    out += self.N[id(b)] @ Z[b.s.off:b.s.off + b.s.size]
+
+        # t's own subtree: its couplings, pushed down with the ancestors' part
+        def bwd(u, cu):
+            v = cu
+            if u is not t:
+                for b in byrow.get(u.id, []):
+                    if b.adm:
+                        w = self.S[id(b)] @ xhat[b.s.id]
+                        v = w if v is None else v + w
+            if u.is_leaf:
+                lo = u.off - t.off
+                if v is not None:
+                    out[lo:lo + u.size] += self.V.leaf[u.id] @ v
+                if u is not t:
+                    for b in byrow.get(u.id, []):
+                        if not b.adm:
+                            out[lo:lo + u.size] += self.N[id(b)] @ Z[b.s.off:b.s.off + b.s.size]
+            else:
+                for ch in u.children:
+                    bwd(ch, None if v is None else self.V.trans[ch.id] @ v)
+        bwd(t, carry)
+        return out
+
+
+def product_block(X, Y, t, r):
+    """(X Y)|_{t x r} (cluster order) of two H^2-matrices sharing the middle
+    cluster tree, through their matrix-vector products: Y on the unit
+    vectors of r (Y|_{J x r}), then the rows t of X applied to it."""
+    return X.rows_matmat(t, Y.matmat_cluster(r, np.eye(r.size)))
+
+
 def chebyshev_basis(root, interp, points):
     leaf, trans, rank = {}, {}, {}
     for c in all_clusters(root):

@@ -567,3 +567,28 @@ def test_work_grows_like_n_log_n():
         fl.append(sum(wk["flops"].values()))
         assert wk["calls"]["gemm"] > 0 and wk["calls"]["qr"] > 0 and wk["calls"]["svd"] > 0
     assert 1.6 < fl[1] / fl[0] < 3.0 and 1.6 < fl[2] / fl[1] < 3.0
+
+
+# ------------------------------------------- restricted matrix products ----
+@pytest.mark.parametrize("w", [I.plain_1d(1000), I.grid_2d(32), I.cube_3d(1200, seed=11, leaf=40, order=2)],
+                         ids=["1d", "2d", "3d"])
+def test_restricted_products_match_dense(w):
+    """The matrix-vector products restricted to one cluster (columns supported
+    in c; rows of t) and the product blocks (XY)|_{t x r} built from them,
+    against the dense matrices (cluster order), for every cluster and the
+    first blocks of the block tree."""
+    X, Y = build_pair(w)
+    Xd, Yd = X.dense_block(X.blocks), Y.dense_block(Y.blocks)
+    rng = np.random.default_rng(21)
+    for c in O.all_clusters(X.rows):
+        Xc = rng.standard_normal((c.size, 3))
+        ref = Xd[:, c.off:c.off + c.size] @ Xc
+        assert np.allclose(X.matmat_cluster(c, Xc), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+        Z = rng.standard_normal((w.n, 2))
+        ref2 = (Xd @ Z)[c.off:c.off + c.size]
+        assert np.allclose(X.rows_matmat(c, Z), ref2, rtol=0, atol=1e-12 * np.abs(ref2).max())
+    Zd = Xd @ Yd
+    for b in O.all_blocks(X.blocks)[:80]:
+        ref = Zd[b.t.off:b.t.off + b.t.size, b.s.off:b.s.off + b.s.size]
+        got = O.product_block(X, Y, b.t, b.s)
+        assert np.allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
