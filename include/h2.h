@@ -238,6 +238,49 @@ int h2_server_submit(h2_server* s, const h2_matrix* A, const h2_matrix* B, doubl
 int h2_server_wait(h2_server* s, int64_t ticket, h2_matrix** C, double* queued_ms, double* total_ms);
 void h2_server_destroy(h2_server* s);
 
+/* ---- Batching: many products in merged launches --------------------------
+ * A batch holds nprod products C_i = A_i * B_i (h2_mul semantics, with the
+ * shared opts and eps[i]; A_i, B_i must stay alive as long as the batch).  The
+ * stage lists of all products (the level-by-level work of Sections 3-5) are
+ * interleaved into one launch sequence: a launch serves the matching stage of
+ * every product whose next stage it is, whatever the products' sizes, ranks
+ * and block counts; runs of consecutive GEMM stages (the tree levels of the
+ * basis products, of the accumulation and of the projections) become one
+ * persistent launch whose CTAs take jobs of all products from a device work
+ * queue, a job waiting (at most about a second, then H2_ETIMEOUT) until its
+ * product's previous level is complete; the whole sequence is captured in one
+ * CUDA graph.  Each product keeps its own workspace and plan, so every result
+ * is bitwise the one h2_mul gives alone.
+ *   h2_batch_create   plans, workspaces and results allocated, graph captured
+ *   h2_batch_run      replays the batch on `stream` (NULL: library stream);
+ *                     sync = 1 waits and returns the first error of a product
+ *   h2_batch_result   the i-th result, owned by the batch: valid until the
+ *                     batch is freed, overwritten by the next run
+ *   h2_batch_info     launches per run (scans counted per product), persistent
+ *                     chains among them, kernel launches of the last enqueue
+ *   h2_batch_autotune times every GEMM launch of the batch with each kernel
+ *                     variant (outputs per thread, tiles per warp) and, for
+ *                     chains, CTAs per SM, pins the fastest per shape class in
+ *                     a process-wide table used by batches created afterwards,
+ *                     and re-captures this batch; the choices never change a
+ *                     result (the arithmetic of a job does not depend on them)
+ *   h2_tuning_table   the pinned table as text (returns its length)
+ * h2_batch_opts.test_unreachable_wait = 1 makes the first chained job wait on
+ * a counter nothing sets (tests of the bounded wait: the run returns
+ * H2_ETIMEOUT after about a second and the batch remains usable). */
+typedef struct h2_batch h2_batch;
+typedef struct {
+  int test_unreachable_wait;
+} h2_batch_opts;
+int h2_batch_create(int nprod, const h2_matrix* const* A, const h2_matrix* const* B, const double* eps,
+                    const h2_mul_opts* opts, const h2_batch_opts* bopts, h2_batch** out);
+int h2_batch_run(h2_batch* b, void* stream, int sync);
+int h2_batch_result(const h2_batch* b, int i, const h2_matrix** C);
+int h2_batch_info(const h2_batch* b, int* launches, int* chains, int* kernel_launches);
+int h2_batch_autotune(h2_batch* b, int* ntuned);
+int h2_tuning_table(char* buf, int len);
+void h2_batch_free(h2_batch* b);
+
 /* Dense n x n column-major expansion (caller ordering) into `out` (host or device). */
 int h2_to_dense(const h2_matrix* A, double* out, int on_device);
 

@@ -17,7 +17,10 @@
 #include <cstring>
 #include <deque>
 #include <list>
+#include <map>
+#include <memory>
 #include <string>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -400,6 +403,7 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
 static int map_err(int dev_err) {
   switch (dev_err) {
     case 0: return H2_OK;
+    case -4: return H2_ETIMEOUT;
     case -5: return H2_ENOCONV;
     case -7: return H2_ERANK;
     default: return H2_EINVAL;
@@ -813,14 +817,11 @@ static int mul_entry(const MulArgs& m, std::shared_ptr<PlanEntry>& e) {
   return H2_OK;
 }
 
-// Enqueues the product on stream s with plan instance rt; *Cout holds C,
-// whose `done` event marks its completion.
-static int enqueue_product(const MulArgs& m, PlanRT& rt, cudaStream_t s, h2_kernel_prof* prof, h2_matrix** Cout) {
+// A new product matrix C for plan P (storage allocated on stream s, its
+// coefficient area cleared).
+static int new_product_matrix(const MulArgs& m, const Plan& P, cudaStream_t s, h2_matrix** Cout) {
   h2_matrix* A = m.A;
   h2_matrix* B = m.B;
-  int rc;
-  if ((rc = ensure_level_bases(A, s)) || (rc = ensure_level_bases(B, s))) return rc;
-  Plan& P = *rt.plan;
   auto C = new h2_matrix();
   C->dim = A->dim;
   C->eta = A->eta;
@@ -851,8 +852,29 @@ static int enqueue_product(const MulArgs& m, PlanRT& rt, cudaStream_t s, h2_kern
     return H2_ENOMEM;
   }
   cudaMemsetAsync(C->d_arena, 0, P.c_len * sizeof(double), s);
-  const double params[PARAM_COUNT] = {m.eps / 4.0 * std::sqrt(1.0 - 2.0 * m.theta), m.eps / 3.0,
-                                       svd_noise_floor(m.eps, m.precision), (double)m.svd_sweeps};
+  *Cout = C;
+  return H2_OK;
+}
+
+// Per-product parameters (scal[0..PARAM_COUNT)).
+static void product_params(const MulArgs& m, double* params) {
+  params[PARAM_TOL_BASIS] = m.eps / 4.0 * std::sqrt(1.0 - 2.0 * m.theta);
+  params[PARAM_TOL_AGG] = m.eps / 3.0;
+  params[PARAM_SVD_FLOOR] = svd_noise_floor(m.eps, m.precision);
+  params[PARAM_SVD_SWEEPS] = (double)m.svd_sweeps;
+}
+
+// Enqueues the product on stream s with plan instance rt; *Cout holds C,
+// whose `done` event marks its completion.
+static int enqueue_product(const MulArgs& m, PlanRT& rt, cudaStream_t s, h2_kernel_prof* prof, h2_matrix** Cout) {
+  h2_matrix* A = m.A;
+  h2_matrix* B = m.B;
+  int rc;
+  if ((rc = ensure_level_bases(A, s)) || (rc = ensure_level_bases(B, s))) return rc;
+  h2_matrix* C = nullptr;
+  if ((rc = new_product_matrix(m, *rt.plan, s, &C))) return rc;
+  double params[PARAM_COUNT];
+  product_params(m, params);
   rc = prof ? run_plan_profiled(rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, prof)
             : run_plan(rt, A->d_arena, B->d_arena, C->d_arena, C->d_int, params, s, true);
   if (rc) {
@@ -1483,3 +1505,542 @@ void h2_server_destroy(h2_server* S) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ batching ----
+// A batch runs many products in merged launches: the stage lists of all its
+// products are interleaved so that one launch serves the matching stage of
+// every product whose next stage it is (one segment per product), runs of
+// consecutive GEMM stages become one persistent launch fed by a device work
+// queue, where a job waits (bounded) for its product's previous stage, and
+// the whole schedule is captured once in a CUDA graph.  Every product keeps
+// its own plan instance (workspace, control block), so the arithmetic of
+// every job is the one of the product run alone: results are bitwise equal.
+namespace h2 {
+namespace {
+
+// Pinned launch choices of the autotuner per GEMM shape class: kernel
+// variant (outputs per thread or tiles per warp) and, for persistent chains,
+// CTAs per SM.  Neither changes the arithmetic of a job.
+struct TuneKey {
+  int mode, slices, mmax, nb, chain;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(mode, slices, mmax, nb, chain) < std::tie(o.mode, o.slices, o.mmax, o.nb, o.chain);
+  }
+};
+struct TuneVal {
+  int variant, ctas_per_sm;
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+struct BatchLaunch {
+  int kind = 0;
+  Stage st{};          // representative stage (GEMM: combined shape in aux)
+  int seg0 = 0, nseg = 0, total = 0;
+  bool chain = false;
+  GemmShape g{};
+  int grid = 0;        // chains: persistent grid
+  int ctr0 = 0, nctr = 0;
+  std::vector<std::pair<int, Stage>> scans;  // per-product scan stages
+};
+
+// Kernel variants a GEMM shape may use: the smallest that fits its largest
+// tile, and the larger ones.
+std::vector<int> gemm_variants(const GemmShape& g) {
+  std::vector<int> v;
+  if (g.slices) {
+    for (int t : {1, 2, 4})
+      if (t >= g.variant) v.push_back(t);
+  } else {
+    for (int q : {1, 4, 16})
+      if (q >= g.variant) v.push_back(q);
+  }
+  return v;
+}
+
+}  // namespace
+}  // namespace h2
+
+struct h2_batch {
+  int n = 0;
+  std::vector<MulArgs> args;
+  std::vector<std::shared_ptr<h2::PlanEntry>> entries;
+  std::vector<std::shared_ptr<h2::PlanRT>> inst;
+  std::vector<h2_matrix*> C;
+  std::vector<h2::BatchLaunch> launches;
+  std::vector<h2::BatchSeg> segs;
+  h2::BatchSeg* d_segs = nullptr;
+  int* d_ctr = nullptr;
+  int nctr = 0;
+  int nsm = 0;
+  int test_wait = 0;
+  int kernel_launches = 0;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t done = nullptr;
+  ~h2_batch() {
+    if (done) cudaEventSynchronize(done);
+    if (graph) cudaGraphExecDestroy(graph);
+    if (done) cudaEventDestroy(done);
+    if (cs) cudaStreamDestroy(cs);
+    cudaFree(d_segs);
+    cudaFree(d_ctr);
+    for (h2_matrix* c : C) h2_free(c);
+  }
+};
+
+using namespace h2;
+
+// Merged launch sequence of the batch: at every step the stage kind (GEMM:
+// with its arithmetic mode; others: with identical launch parameters) that is
+// next for the most products runs for all of them; then consecutive GEMM
+// launches of one mode are fused into persistent chains.
+static int batch_schedule(h2_batch* b) {
+  const int P = b->n;
+  std::vector<size_t> cur(P, 0);
+  b->launches.clear();
+  b->segs.clear();
+  b->nctr = 0;
+  auto key_of = [](const Stage& st) {
+    if (st.kind == ST_GEMM) {
+      const GemmShape g = gemm_shape(st.aux);
+      return std::make_tuple((int)ST_GEMM, g.mode * 16 + g.slices, 0);
+    }
+    return std::make_tuple(st.kind, st.smem, st.aux);
+  };
+  for (;;) {
+    std::map<std::tuple<int, int, int>, std::pair<int, size_t>> cand;
+    for (int p = 0; p < P; ++p) {
+      const auto& stages = b->inst[p]->plan->stages;
+      if (cur[p] >= stages.size()) continue;
+      auto& c = cand[key_of(stages[cur[p]])];
+      c.first += 1;
+      c.second = std::max(c.second, stages.size() - cur[p]);
+    }
+    if (cand.empty()) break;
+    auto best = cand.begin();
+    for (auto it = cand.begin(); it != cand.end(); ++it)
+      if (it->second > best->second) best = it;
+    const auto key = best->first;
+    BatchLaunch L;
+    L.kind = std::get<0>(key);
+    L.seg0 = (int)b->segs.size();
+    int mmax = 1, nb = 1, flags = 0;
+    for (int p = 0; p < P; ++p) {
+      const auto& stages = b->inst[p]->plan->stages;
+      if (cur[p] >= stages.size() || key_of(stages[cur[p]]) != key) continue;
+      const Stage& st = stages[cur[p]++];
+      if (st.count <= 0) continue;
+      if (L.nseg == 0) L.st = st;
+      const PlanRT& rt = *b->inst[p];
+      if (L.kind == ST_SCAN) {
+        L.scans.emplace_back(p, st);
+        continue;
+      }
+      BatchSeg sg{};
+      sg.ctx = rt.d_ctx;
+      switch (st.kind) {
+        case ST_GEMM: sg.jobs = rt.dj.gemm_out + st.first; break;
+        case ST_COPY: sg.jobs = rt.dj.copy + st.first; break;
+        case ST_QR: sg.jobs = rt.dj.qr + st.first; break;
+        case ST_QAPPLY: sg.jobs = rt.dj.qapply + st.first; break;
+        case ST_SVD: sg.jobs = rt.dj.svd + st.first; break;
+        case ST_NORM: sg.jobs = rt.dj.norm + st.first; break;
+        default: break;
+      }
+      sg.terms = rt.dj.gemm_term;
+      sg.start = L.total;
+      sg.count = st.count;
+      sg.wait_idx = sg.wait_target = sg.done_idx = -1;
+      sg.first = (int)st.first;
+      sg.done_idx = p;  // product index, replaced by a counter in chains
+      L.total += st.count;
+      b->segs.push_back(sg);
+      ++L.nseg;
+      if (st.kind == ST_GEMM) {
+        const GemmShape g = gemm_shape(st.aux);
+        mmax = std::max(mmax, g.mmax);
+        nb = std::max(nb, g.nb);
+        flags = st.aux & GEMM_AUX_FLAGS;
+      }
+    }
+    if (L.kind == ST_SCAN) {
+      if (!L.scans.empty()) b->launches.push_back(L);
+      continue;
+    }
+    if (L.nseg == 0) continue;
+    if (L.kind == ST_GEMM) {
+      L.st.aux = (mmax << 16) | nb | flags;
+      L.g = gemm_shape(L.st.aux);
+    }
+    b->launches.push_back(L);
+  }
+  // fuse runs of GEMM launches of one mode into chains
+  std::vector<BatchLaunch> out;
+  std::vector<BatchSeg> segs;
+  for (size_t i = 0; i < b->launches.size();) {
+    BatchLaunch& L = b->launches[i];
+    size_t j = i + 1;
+    if (L.kind == ST_GEMM)
+      while (j < b->launches.size() && b->launches[j].kind == ST_GEMM &&
+             (b->launches[j].st.aux & GEMM_AUX_FLAGS) == (L.st.aux & GEMM_AUX_FLAGS))
+        ++j;
+    if (L.kind != ST_GEMM || j - i < 2) {
+      BatchLaunch M = L;
+      M.seg0 = (int)segs.size();
+      for (int k = 0; k < L.nseg; ++k) segs.push_back(b->segs[L.seg0 + k]);
+      out.push_back(M);
+      i = j;
+      continue;
+    }
+    BatchLaunch Ch;
+    Ch.kind = ST_GEMM;
+    Ch.chain = true;
+    Ch.seg0 = (int)segs.size();
+    Ch.ctr0 = b->nctr;
+    int mmax = 1, nb = 1;
+    // counters of a chain, relative to its base ctr0: 0 the work queue, then
+    // one done counter per segment
+    std::map<int, std::pair<int, int>> last;  // product -> (done counter, count) of its latest chain stage
+    int nextc = 1;
+    for (size_t l = i; l < j; ++l) {
+      const BatchLaunch& G = b->launches[l];
+      mmax = std::max(mmax, G.g.mmax);
+      nb = std::max(nb, G.g.nb);
+      for (int k = 0; k < G.nseg; ++k) {
+        BatchSeg sg = b->segs[G.seg0 + k];
+        const int p = sg.done_idx;
+        sg.start = Ch.total;
+        auto it = last.find(p);
+        if (it != last.end()) {
+          sg.wait_idx = it->second.first;
+          sg.wait_target = it->second.second;
+        } else {
+          sg.wait_idx = sg.wait_target = -1;
+        }
+        sg.done_idx = nextc;
+        last[p] = {nextc, sg.count};
+        ++nextc;
+        Ch.total += sg.count;
+        segs.push_back(sg);
+        ++Ch.nseg;
+      }
+    }
+    Ch.nctr = nextc;
+    b->nctr = Ch.ctr0 + nextc;
+    Ch.st = b->launches[i].st;
+    Ch.st.aux = (mmax << 16) | nb | (Ch.st.aux & GEMM_AUX_FLAGS);
+    Ch.g = gemm_shape(Ch.st.aux);
+    out.push_back(Ch);
+    i = j;
+  }
+  for (auto& M : out)
+    if (!M.chain)
+      for (int k = 0; k < M.nseg; ++k) segs[M.seg0 + k].done_idx = -1;
+  // test hook: the first chain's first job waits on a counter nothing sets
+  // (one past every chain's counters; zeroed once at upload, never written)
+  if (b->test_wait) {
+    for (auto& M : out)
+      if (M.chain) {
+        segs[M.seg0].wait_idx = b->nctr - M.ctr0;
+        segs[M.seg0].wait_target = 1;
+        ++b->nctr;
+        break;
+      }
+  }
+  b->launches.swap(out);
+  b->segs.swap(segs);
+  // pinned launch choices, persistent grids
+  for (auto& M : b->launches) {
+    if (M.kind != ST_GEMM) continue;
+    int cps = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(TuneKey{M.g.mode, M.g.slices, M.g.mmax, M.g.nb, M.chain ? 1 : 0});
+      if (it != g_tune.end()) {
+        M.g.variant = it->second.variant;
+        cps = it->second.ctas_per_sm;
+      }
+    }
+    if (M.chain) {
+      const int occ = gemm_chain_blocks_per_sm(M.g);
+      if (occ <= 0) return H2_ECUDA;
+      const int c = cps > 0 ? std::min(cps, occ) : occ;
+      M.grid = std::min(M.total, c * b->nsm);
+    }
+  }
+  return H2_OK;
+}
+
+// Enqueues the batch's launches (graph capture or direct).  tgt: per launch
+// the (variant, ctas per SM) to use instead of the scheduled ones (tuning),
+// ev: events around every GEMM launch (tuning).
+static void batch_enqueue(h2_batch* b, cudaStream_t s, const std::vector<std::pair<int, int>>* tgt,
+                          std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
+  b->kernel_launches = 0;
+  for (int p = 0; p < b->n; ++p) {
+    const PlanRT& rt = *b->inst[p];
+    const Plan& P = *rt.plan;
+    cudaMemsetAsync(b->C[p]->d_arena, 0, P.c_len * sizeof(double), s);
+    if (!P.slot_init.empty())
+      cudaMemcpyAsync(rt.d_slot, rt.d_slot_init, sizeof(int) * P.slot_init.size(), cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(rt.d_err, 0, sizeof(int), s);
+  }
+  for (size_t l = 0; l < b->launches.size(); ++l) {
+    const BatchLaunch& L = b->launches[l];
+    if (L.kind == ST_SCAN) {
+      for (const auto& ps : L.scans) {
+        launch_stage(ps.second, b->inst[ps.first]->d_ctx, b->inst[ps.first]->dj, s);
+        ++b->kernel_launches;
+      }
+      continue;
+    }
+    GemmShape g = L.g;
+    int grid = L.grid;
+    if (L.kind == ST_GEMM && tgt) {
+      g.variant = (*tgt)[l].first;
+      if (L.chain) {
+        const int occ = gemm_chain_blocks_per_sm(g);
+        grid = std::min(L.total, std::max(1, std::min((*tgt)[l].second, occ)) * b->nsm);
+      }
+    }
+    if (ev && L.kind == ST_GEMM) cudaEventRecord((*ev)[l].first, s);
+    if (L.chain) {
+      cudaMemsetAsync(b->d_ctr + L.ctr0, 0, sizeof(int) * L.nctr, s);
+      launch_gemm_chain(g, grid, b->d_segs + L.seg0, L.nseg, L.total, b->d_ctr + L.ctr0, s);
+      ++b->kernel_launches;
+    } else if (L.kind == ST_GEMM) {
+      launch_gemm_batched(g, b->d_segs + L.seg0, L.nseg, L.total, s);
+      ++b->kernel_launches;
+    } else {
+      launch_stage_batched(L.st, b->d_segs + L.seg0, L.nseg, L.total, s);
+      b->kernel_launches += stage_launches(L.st);
+    }
+    if (ev && L.kind == ST_GEMM) cudaEventRecord((*ev)[l].second, s);
+  }
+  for (int p = 0; p < b->n; ++p) {
+    launch_finalize(b->inst[p]->d_ctx, b->inst[p]->nrank, s);
+    ++b->kernel_launches;
+  }
+}
+
+static int batch_capture(h2_batch* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+  batch_enqueue(b, b->cs, nullptr, nullptr);
+  cudaError_t e = cudaStreamEndCapture(b->cs, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "batch capture");
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "batch instantiate");
+  return H2_OK;
+}
+
+static int batch_upload(h2_batch* b) {
+  cudaFree(b->d_segs);
+  cudaFree(b->d_ctr);
+  b->d_segs = nullptr;
+  b->d_ctr = nullptr;
+  CK(cudaMalloc(&b->d_segs, std::max<size_t>(b->segs.size(), 1) * sizeof(BatchSeg)));
+  if (!b->segs.empty())
+    CK(cudaMemcpy(b->d_segs, b->segs.data(), b->segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&b->d_ctr, std::max(b->nctr, 1) * sizeof(int)));
+  CK(cudaMemset(b->d_ctr, 0, std::max(b->nctr, 1) * sizeof(int)));
+  return H2_OK;
+}
+
+int h2_batch_create(int nprod, const h2_matrix* const* A, const h2_matrix* const* B, const double* eps,
+                    const h2_mul_opts* opts, const h2_batch_opts* bopts, h2_batch** out) {
+  if (!out) return H2_EINVAL;
+  *out = nullptr;
+  if (nprod < 1 || nprod > 4096 || !A || !B || !eps) return H2_EINVAL;
+  int rc = lib_init();
+  if (rc) return rc;
+  auto b = std::make_unique<h2_batch>();
+  b->n = nprod;
+  b->test_wait = bopts ? bopts->test_unreachable_wait : 0;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+  for (int p = 0; p < nprod; ++p) {
+    MulArgs m;
+    if ((rc = mul_args(A[p], B[p], eps[p], opts, m))) return rc;
+    std::shared_ptr<PlanEntry> e;
+    if ((rc = mul_entry(m, e))) return rc;
+    std::shared_ptr<PlanRT> base;
+    {
+      std::lock_guard<std::mutex> lk(e->mu);
+      base = e->inst[0];
+    }
+    std::shared_ptr<PlanRT> rt;  // a workspace of its own for every product of the batch
+    if ((rc = clone_instance(base, rt))) return rc;
+    if ((rc = ensure_level_bases(m.A, g_stream)) || (rc = ensure_level_bases(m.B, g_stream))) return rc;
+    h2_matrix* C = nullptr;
+    if ((rc = new_product_matrix(m, *rt->plan, g_stream, &C))) return rc;
+    b->C.push_back(C);
+    CK(cudaEventCreateWithFlags(&C->done, cudaEventDisableTiming));
+    // control block: fixed for the batch's lifetime
+    ExecCtx ctx{};
+    const Plan& P = *rt->plan;
+    ctx.base[AR_WS] = rt->d_ws;
+    ctx.base[AR_X] = m.A->d_arena;
+    ctx.base[AR_Y] = m.B->d_arena;
+    ctx.base[AR_C] = C->d_arena;
+    ctx.base[AR_K] = rt->d_konst;
+    ctx.base[AR_F] = rt->d_ws + P.ws_len;
+    ctx.slot = rt->d_slot;
+    ctx.scal = rt->d_scal;
+    ctx.nrm = rt->d_nrm;
+    ctx.err = rt->d_err;
+    ctx.idx = rt->d_idx;
+    ctx.out_int = C->d_int;
+    ctx.rank_src = rt->d_rank_src;
+    ctx.nrank = rt->nrank;
+    double params[PARAM_COUNT];
+    product_params(m, params);
+    std::vector<char> h(512 + sizeof(double) * PARAM_COUNT, 0);
+    std::memcpy(h.data(), &ctx, sizeof(ctx));
+    std::memcpy(h.data() + 512, params, sizeof(params));
+    CK(cudaStreamSynchronize(g_stream));
+    CK(cudaMemcpy(rt->d_ctrl, h.data(), h.size(), cudaMemcpyHostToDevice));
+    b->args.push_back(m);
+    b->entries.push_back(e);
+    b->inst.push_back(rt);
+  }
+  if ((rc = batch_schedule(b.get())) || (rc = batch_upload(b.get())) || (rc = batch_capture(b.get()))) return rc;
+  *out = b.release();
+  return H2_OK;
+}
+
+int h2_batch_run(h2_batch* b, void* stream, int sync) {
+  if (!b) return H2_EINVAL;
+  cudaStream_t s = stream ? (cudaStream_t)stream : g_stream;
+  for (int p = 0; p < b->n; ++p) {
+    if (b->args[p].A->done) CK(cudaStreamWaitEvent(s, b->args[p].A->done, 0));
+    if (b->args[p].B->done) CK(cudaStreamWaitEvent(s, b->args[p].B->done, 0));
+    std::lock_guard<std::mutex> lk(b->C[p]->mu);
+    b->C[p]->levels_ready = false;  // the level bases of a result are rebuilt if it is used as an operand
+  }
+  CK(cudaGraphLaunch(b->graph, s));
+  for (int p = 0; p < b->n; ++p) CK(cudaEventRecord(b->C[p]->done, s));
+  CK(cudaEventRecord(b->done, s));
+  if (!sync) return H2_OK;
+  CK(cudaEventSynchronize(b->done));
+  for (int p = 0; p < b->n; ++p) {
+    const int rc = h2_check(b->C[p]);
+    if (rc) return rc;
+  }
+  return H2_OK;
+}
+
+int h2_batch_result(const h2_batch* b, int i, const h2_matrix** C) {
+  if (!b || !C || i < 0 || i >= b->n) return H2_EINVAL;
+  *C = b->C[i];
+  return H2_OK;
+}
+
+int h2_batch_info(const h2_batch* b, int* launches, int* chains, int* kernel_launches) {
+  if (!b) return H2_EINVAL;
+  int nl = 0, nc = 0;
+  for (const auto& L : b->launches) {
+    nl += L.kind == ST_SCAN ? (int)L.scans.size() : 1;
+    nc += L.chain ? 1 : 0;
+  }
+  if (launches) *launches = nl;
+  if (chains) *chains = nc;
+  if (kernel_launches) *kernel_launches = b->kernel_launches;
+  return H2_OK;
+}
+
+int h2_batch_autotune(h2_batch* b, int* ntuned) {
+  if (!b) return H2_EINVAL;
+  CK(cudaEventSynchronize(b->done));
+  const size_t nl = b->launches.size();
+  // candidates per GEMM launch: variants x (chains) CTAs per SM
+  std::vector<std::vector<std::pair<int, int>>> cand(nl);
+  size_t ncand = 1;
+  for (size_t l = 0; l < nl; ++l) {
+    const BatchLaunch& L = b->launches[l];
+    if (L.kind != ST_GEMM) continue;
+    GemmShape g0 = gemm_shape(L.st.aux);
+    for (int v : gemm_variants(g0)) {
+      if (!L.chain) {
+        cand[l].push_back({v, 0});
+        continue;
+      }
+      GemmShape g = g0;
+      g.variant = v;
+      const int occ = gemm_chain_blocks_per_sm(g);
+      for (int c = 1; c <= occ; c = (c < occ && 2 * c > occ) ? occ : 2 * c) cand[l].push_back({v, c});
+    }
+    ncand = std::max(ncand, cand[l].size());
+  }
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev(nl);
+  for (auto& e : ev) {
+    CK(cudaEventCreate(&e.first));
+    CK(cudaEventCreate(&e.second));
+  }
+  std::vector<std::vector<float>> ms(nl, std::vector<float>(ncand, 1e30f));
+  std::vector<std::pair<int, int>> tgt(nl, {1, 1});
+  for (size_t c = 0; c < ncand; ++c) {
+    for (size_t l = 0; l < nl; ++l)
+      if (!cand[l].empty()) tgt[l] = cand[l][std::min(c, cand[l].size() - 1)];
+    batch_enqueue(b, b->cs, &tgt, &ev);
+    CK(cudaStreamSynchronize(b->cs));
+    for (size_t l = 0; l < nl; ++l)
+      if (!cand[l].empty() && c < cand[l].size()) CK(cudaEventElapsedTime(&ms[l][c], ev[l].first, ev[l].second));
+  }
+  for (auto& e : ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  int nt = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (size_t l = 0; l < nl; ++l) {
+      if (cand[l].empty()) continue;
+      size_t best = 0;
+      for (size_t c = 1; c < cand[l].size(); ++c)
+        if (ms[l][c] < ms[l][best]) best = c;
+      const BatchLaunch& L = b->launches[l];
+      const GemmShape g0 = gemm_shape(L.st.aux);
+      const TuneKey k{g0.mode, g0.slices, g0.mmax, g0.nb, L.chain ? 1 : 0};
+      auto it = g_tune.find(k);
+      if (it == g_tune.end() || ms[l][best] < it->second.ms) {  // a class keeps its fastest choice seen
+        g_tune[k] = TuneVal{cand[l][best].first, cand[l][best].second, ms[l][best]};
+        ++nt;
+      }
+    }
+  }
+  if (ntuned) *ntuned = nt;
+  int rc;
+  if ((rc = batch_schedule(b)) || (rc = batch_upload(b)) || (rc = batch_capture(b))) return rc;
+  return H2_OK;
+}
+
+int h2_tuning_table(char* buf, int len) {
+  std::string s;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : g_tune) {
+      char line[160];
+      std::snprintf(line, sizeof line, "mode %d slices %d tile %dx%d %s: variant %d ctas/SM %d (%.3f ms)\n",
+                    kv.first.mode, kv.first.slices, kv.first.mmax, kv.first.nb, kv.first.chain ? "chain" : "stage",
+                    kv.second.variant, kv.second.ctas_per_sm, kv.second.ms);
+      s += line;
+    }
+  }
+  if (buf && len > 0) {
+    std::snprintf(buf, (size_t)len, "%s", s.c_str());
+  }
+  return (int)s.size();
+}
+
+void h2_batch_free(h2_batch* b) { delete b; }

@@ -279,18 +279,16 @@ __host__ __device__ constexpr int gemm_smem_doubles(int mmax, int nb) {
 // stages take a small Q, so fewer registers and more resident CTAs per SM.
 // MODE = compute mode (above).
 template <int Q, int MODE>
-__global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs,
-                                              const GemmTerm* __restrict__ terms, int mmax, int nb) {
+__device__ __forceinline__ void gemm_job(const ExecCtx& x, const GemmOut& O, const GemmTerm* __restrict__ terms,
+                                         int mmax, int nb) {
   using P = GemmPol<MODE>;
   using S = typename P::S;
-  const ExecCtx& x = *px;
   extern __shared__ double sm_raw[];
   S* sm = reinterpret_cast<S*>(sm_raw);
   const int ldbs = nb + 1;
   S* As = sm;                      // mmax x (GK+1)
   S* Bs = As + mmax * (GK + 1);    // GK x (nb+1)
   S* Ts = Bs + GK * ldbs;          // mmax x (nb+1)
-  const GemmOut& O = outs[blockIdx.x];
   const int m = dimv(O.m, x.slot);
   const int n = O.clampn ? min(dimv(O.n, x.slot), GT) : dimv(O.n, x.slot);
   if (m <= 0 || n <= 0) return;
@@ -365,6 +363,87 @@ __global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2) k_gemm(const
       const double v = P::result(acc[q]);
       *p = O.beta ? (*p + v) : v;
     }
+}
+
+// Index of the segment holding block / queue index b (segments sorted by start).
+__device__ __forceinline__ int seg_find(const BatchSeg* __restrict__ segs, int nseg, int b) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].start <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One CTA per output tile of a stage (segs == nullptr: the jobs of one
+// product; else the segments of a batched launch).
+template <int Q, int MODE>
+__global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2)
+    k_gemm(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs, const GemmTerm* __restrict__ terms,
+           int mmax, int nb, const BatchSeg* __restrict__ segs, int nseg) {
+  int b = blockIdx.x;
+  if (segs) {
+    const BatchSeg& sg = segs[seg_find(segs, nseg, b)];
+    px = sg.ctx;
+    outs = static_cast<const GemmOut*>(sg.jobs);
+    terms = sg.terms;
+    b -= sg.start;
+  }
+  gemm_job<Q, MODE>(*px, outs[b], terms, mmax, nb);
+}
+
+// Bounded wait of a chained job for its product's previous stage: about a
+// second (2^20 polls, 1 us apart), after which the caller records H2_ETIMEOUT.
+constexpr int CHAIN_WAIT_POLLS = 1 << 20;
+__device__ __forceinline__ bool chain_wait(const int* p, int target) {
+  for (int i = 0; i < CHAIN_WAIT_POLLS; ++i) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    if (v >= target) return true;
+    __nanosleep(1000);
+  }
+  return false;
+}
+
+// Persistent launch over a chain of GEMM stages of many products: CTAs take
+// jobs from a device work queue (ctr[0]) in stage order; a job waits for its
+// product's previous stage (BatchSeg::wait_idx) and counts itself done.  The
+// grid never exceeds the CTAs resident at once, so every awaited job is held
+// by a running CTA.  A wait that gives up sets H2_ETIMEOUT (-4) on the
+// product and the job is skipped; the chain still completes.
+template <class JOB>
+__device__ __forceinline__ void chain_loop(const BatchSeg* __restrict__ segs, int nseg, int total, int* ctr, JOB job) {
+  __shared__ int s_job, s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(&ctr[0], 1);
+    __syncthreads();
+    const int j = s_job;
+    if (j >= total) break;
+    const BatchSeg& sg = segs[seg_find(segs, nseg, j)];
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      if (sg.wait_idx >= 0) ok = chain_wait(&ctr[sg.wait_idx], sg.wait_target) ? 1 : 0;
+      if (!ok) set_err(*sg.ctx, -4);
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) job(sg, j - sg.start);
+    __syncthreads();
+    if (threadIdx.x == 0 && sg.done_idx >= 0) {
+      __threadfence();
+      atomicAdd(&ctr[sg.done_idx], 1);
+    }
+  }
+}
+
+template <int Q, int MODE>
+__global__ void __launch_bounds__(256, Q == 1 ? 5 : Q == 4 ? 4 : 2)
+    k_gemm_chain(const BatchSeg* __restrict__ segs, int nseg, int total, int* ctr, int mmax, int nb) {
+  chain_loop(segs, nseg, total, ctr, [&](const BatchSeg& sg, int i) {
+    gemm_job<Q, MODE>(*sg.ctx, static_cast<const GemmOut*>(sg.jobs)[i], sg.terms, mmax, nb);
+  });
 }
 
 // ------------------------------------------------- tensor-core GEMM (BF16) ----
@@ -670,10 +749,8 @@ __device__ void tc_product(DF (&acc)[TPW][4], float2* ts, int ldts, const TcSrc&
 // shared memory (when the stage has such terms: shared memory for them is
 // part of the launch), then adds alpha Ts op(C).
 template <int S, int TPW>
-__global__ void __launch_bounds__(256, 2)
-    k_gemm_tc(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs, const GemmTerm* __restrict__ terms,
-              int mmax, int nb) {
-  const ExecCtx& x = *px;
+__device__ __forceinline__ void gemm_tc_job(const ExecCtx& x, const GemmOut& O, const GemmTerm* __restrict__ terms,
+                                            int mmax, int nb) {
   extern __shared__ __align__(16) unsigned char tc_raw[];
   const int m16max = (mmax + 15) & ~15, n8max = (nb + 7) & ~7;
   uint16_t* As = reinterpret_cast<uint16_t*>(tc_raw);
@@ -682,7 +759,6 @@ __global__ void __launch_bounds__(256, 2)
   int* cexp = rexp + 64;
   float2* Ts = reinterpret_cast<float2*>(cexp + 64);
   const int ldts = nb + 1;
-  const GemmOut& O = outs[blockIdx.x];
   const int m = dimv(O.m, x.slot);
   const int n = O.clampn ? min(dimv(O.n, x.slot), GT) : dimv(O.n, x.slot);
   if (m <= 0 || n <= 0) return;
@@ -757,15 +833,46 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
+template <int S, int TPW>
+__global__ void __launch_bounds__(256, 2)
+    k_gemm_tc(const ExecCtx* __restrict__ px, const GemmOut* __restrict__ outs, const GemmTerm* __restrict__ terms,
+              int mmax, int nb, const BatchSeg* __restrict__ segs, int nseg) {
+  int b = blockIdx.x;
+  if (segs) {
+    const BatchSeg& sg = segs[seg_find(segs, nseg, b)];
+    px = sg.ctx;
+    outs = static_cast<const GemmOut*>(sg.jobs);
+    terms = sg.terms;
+    b -= sg.start;
+  }
+  gemm_tc_job<S, TPW>(*px, outs[b], terms, mmax, nb);
+}
+
+template <int S, int TPW>
+__global__ void __launch_bounds__(256, 2)
+    k_gemm_tc_chain(const BatchSeg* __restrict__ segs, int nseg, int total, int* ctr, int mmax, int nb) {
+  chain_loop(segs, nseg, total, ctr, [&](const BatchSeg& sg, int i) {
+    gemm_tc_job<S, TPW>(*sg.ctx, static_cast<const GemmOut*>(sg.jobs)[i], sg.terms, mmax, nb);
+  });
+}
+
 // Dynamic shared memory of a tensor-core GEMM stage (bytes).
 __host__ __device__ constexpr int gemm_tc_smem_bytes(int S, int mmax, int nb) {
   return 2 * S * (((mmax + 15) & ~15) + ((nb + 7) & ~7)) * TKP + 2 * 64 * 4 + 8 * mmax * (nb + 1);
 }
 
 // ------------------------------------------------------------------ copy ----
-__global__ void __launch_bounds__(256) k_copy(const ExecCtx* __restrict__ px, const CopyJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) k_copy(const ExecCtx* __restrict__ px, const CopyJob* __restrict__ jobs,
+                                              const BatchSeg* __restrict__ segs, int nseg) {
+  int jb = blockIdx.x;
+  if (segs) {
+    const BatchSeg& sg = segs[seg_find(segs, nseg, jb)];
+    px = sg.ctx;
+    jobs = static_cast<const CopyJob*>(sg.jobs);
+    jb -= sg.start;
+  }
   const ExecCtx& x = *px;
-  const CopyJob& J = jobs[blockIdx.x];
+  const CopyJob& J = jobs[jb];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
   const int zr = max(rows, dimv(J.zrows, x.slot)), zc = max(cols, dimv(J.zcols, x.slot));
   const double* S = ptrv(J.src, x);
@@ -1154,12 +1261,19 @@ __device__ void write_r(const QrJob& J, double* r, const double* src, int64_t ld
 }
 
 __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, const QrJob* __restrict__ jobs,
-                                            int smem_doubles) {
+                                            int smem_doubles, const BatchSeg* __restrict__ segs, int nseg) {
+  int jb = blockIdx.x;
+  if (segs) {
+    const BatchSeg& sg = segs[seg_find(segs, nseg, jb)];
+    px = sg.ctx;
+    jobs = static_cast<const QrJob*>(sg.jobs);
+    jb -= sg.start;
+  }
   const ExecCtx& x = *px;
   extern __shared__ double sm[];
   __shared__ double sh[2];
   __shared__ double cn[QR_MAXPIV], cn0[QR_MAXPIV];
-  const QrJob& J = jobs[blockIdx.x];
+  const QrJob& J = jobs[jb];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
   double* a = ptrv(J.a, x);
   double* tau = ptrv(J.tau, x);
@@ -1230,12 +1344,20 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
 // the columns); the block's reflector products v_k^T v_m are one warp each.
 // A block reads and writes out once and takes three barriers, not QB times.
 constexpr int QB = 4;
-__global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, const QApplyJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, const QApplyJob* __restrict__ jobs,
+                                                const BatchSeg* __restrict__ segs, int nsegs) {
+  int jb = blockIdx.x;
+  if (segs) {
+    const BatchSeg& sg = segs[seg_find(segs, nsegs, jb)];
+    px = sg.ctx;
+    jobs = static_cast<const QApplyJob*>(sg.jobs);
+    jb -= sg.start;
+  }
   const ExecCtx& x = *px;
   __shared__ double part[QB][256];
   __shared__ double wsh[QB][256];
   __shared__ double gsh[QB * QB];
-  const QApplyJob& J = jobs[blockIdx.x];
+  const QApplyJob& J = jobs[jb];
   const int rows = dimv(J.rows, x.slot), q = dimv(J.q, x.slot), nc = dimv(J.ncols, x.slot);
   const double* a = ptrv(J.a, x);
   const double* tau = ptrv(J.tau, x);
@@ -1350,7 +1472,16 @@ __device__ __forceinline__ int svd_pair_j(int rnd, int p, int ce) {
 // (need_lo, need_hi]: a stage of mixed sizes then runs its small jobs in
 // small CTAs, many per SM, and its large ones in a second launch.
 __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, const SvdJob* __restrict__ jobs,
-                                                int64_t first, int smem_doubles, int cmax, int need_lo, int need_hi) {
+                                                int64_t first, int smem_doubles, int cmax, int need_lo, int need_hi,
+                                                const BatchSeg* __restrict__ segs, int nsegs) {
+  int jb = blockIdx.x;
+  if (segs) {
+    const BatchSeg& sg = segs[seg_find(segs, nsegs, jb)];
+    px = sg.ctx;
+    jobs = static_cast<const SvdJob*>(sg.jobs);
+    jb -= sg.start;
+    first = sg.first;
+  }
   const ExecCtx& x = *px;
   extern __shared__ double sdyn[];
   __shared__ int rotated;
@@ -1358,7 +1489,7 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
   __shared__ int nround;
   __shared__ double part[256];  // partial dot products (blockDim <= 256)
   __shared__ double s_fro;
-  const SvdJob& J = jobs[blockIdx.x];
+  const SvdJob& J = jobs[jb];
   const int rows = dimv(J.rows, x.slot), cols = dimv(J.cols, x.slot);
   {
     const int64_t need = (rows <= 0 || cols <= 0) ? 0 : svd_colarr_doubles(cols) + (int64_t)(rows + 1) * cols;
@@ -1543,8 +1674,8 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
   if (threadIdx.x == 0) {
     if (sweep >= maxsweep) set_err(x, -5);
     if (x.svd_sweeps) {
-      x.svd_sweeps[2 * (first + blockIdx.x)] = sweep + 1;
-      x.svd_sweeps[2 * (first + blockIdx.x) + 1] = nrot;
+      x.svd_sweeps[2 * (first + jb)] = sweep + 1;
+      x.svd_sweeps[2 * (first + jb) + 1] = nrot;
     }
   }
   // singular values = column norms (exact), sorted descending
@@ -1606,14 +1737,21 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
 // G lives in dynamic shared memory sized for the stage's largest n (nmax x
 // (nmax+1) doubles); N is read from global memory (L1-resident).
 __global__ void __launch_bounds__(256) k_norm(const ExecCtx* __restrict__ px, const NormJob* __restrict__ jobs,
-                                              int nmax) {
+                                              int nmax, const BatchSeg* __restrict__ segs, int nseg) {
+  int jb = blockIdx.x;
+  if (segs) {
+    const BatchSeg& sg = segs[seg_find(segs, nseg, jb)];
+    px = sg.ctx;
+    jobs = static_cast<const NormJob*>(sg.jobs);
+    jb -= sg.start;
+  }
   const ExecCtx& x = *px;
   constexpr int NM = NORM_MAXN;
   extern __shared__ double G[];  // nmax x (nmax+1)
   __shared__ double v[NM], p[NM], w[NM], d[NM], e[NM];
   __shared__ double red[32];
   __shared__ double sh[4];
-  const NormJob& J = jobs[blockIdx.x];
+  const NormJob& J = jobs[jb];
   const int n = dimv(J.n, x.slot);
   if (n <= 0 || n > nmax || n > NM) {
     if (threadIdx.x == 0) {
@@ -1773,12 +1911,35 @@ cudaError_t kernels_init() {
   H2_GEMM_ATTR(1, GM_F32) H2_GEMM_ATTR(4, GM_F32) H2_GEMM_ATTR(GQ, GM_F32)
   H2_GEMM_ATTR(1, GM_DF) H2_GEMM_ATTR(4, GM_DF) H2_GEMM_ATTR(GQ, GM_DF)
 #undef H2_GEMM_ATTR
+#define H2_GEMM_ATTR_CHAIN                                                                          \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<1, GM_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<4, GM_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<GQ, GM_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<1, GM_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<4, GM_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<GQ, GM_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<1, GM_DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<4, GM_DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_chain<GQ, GM_DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm); \
+  for (int S_ : {5, 7}) {                                                                            \
+    const int tsm = gemm_tc_smem_bytes(S_, GT, GT);                                                  \
+    if (S_ == 5) {                                                                                   \
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc_chain<5, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm); \
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc_chain<5, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm); \
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc_chain<5, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm); \
+    } else {                                                                                         \
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc_chain<7, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm); \
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc_chain<7, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm); \
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc_chain<7, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm); \
+    }                                                                                                \
+  }
 #define H2_GEMM_TC_ATTR(S, T)                                                                      \
   if (e == cudaSuccess)                                                                            \
     e = cudaFuncSetAttribute(k_gemm_tc<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
                              gemm_tc_smem_bytes(S, GT, GT));
   H2_GEMM_TC_ATTR(5, 1) H2_GEMM_TC_ATTR(5, 2) H2_GEMM_TC_ATTR(5, 4)
   H2_GEMM_TC_ATTR(7, 1) H2_GEMM_TC_ATTR(7, 2) H2_GEMM_TC_ATTR(7, 4)
+  H2_GEMM_ATTR_CHAIN
 #undef H2_GEMM_TC_ATTR
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)norm_smem_bytes(NORM_MAXN));
@@ -1799,72 +1960,88 @@ void launch_finalize(const ExecCtx* x, int nrank, cudaStream_t s) {
 // qsteps = ceil(mmax / (256 / nb)): outputs per thread of the stage's largest tile
 template <int MODE>
 static void launch_gemm_mode(int qsteps, int count, size_t sm, cudaStream_t s, const ExecCtx* x, const GemmOut* go,
-                             const GemmTerm* gt, int mmax, int nb) {
+                             const GemmTerm* gt, int mmax, int nb, const BatchSeg* segs, int nseg) {
   if (qsteps <= 1)
-    k_gemm<1, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+    k_gemm<1, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb, segs, nseg);
   else if (qsteps <= 4)
-    k_gemm<4, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+    k_gemm<4, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb, segs, nseg);
   else
-    k_gemm<GQ, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+    k_gemm<GQ, MODE><<<count, 256, sm, s>>>(x, go, gt, mmax, nb, segs, nseg);
 }
 
 static void launch_gemm(int mode, int qsteps, int count, size_t sm, cudaStream_t s, const ExecCtx* x,
-                        const GemmOut* go, const GemmTerm* gt, int mmax, int nb) {
+                        const GemmOut* go, const GemmTerm* gt, int mmax, int nb, const BatchSeg* segs, int nseg) {
   if (mode == GM_DF)
-    launch_gemm_mode<GM_DF>(qsteps, count, sm, s, x, go, gt, mmax, nb);
+    launch_gemm_mode<GM_DF>(qsteps, count, sm, s, x, go, gt, mmax, nb, segs, nseg);
   else if (mode == GM_F32)
-    launch_gemm_mode<GM_F32>(qsteps, count, sm, s, x, go, gt, mmax, nb);
+    launch_gemm_mode<GM_F32>(qsteps, count, sm, s, x, go, gt, mmax, nb, segs, nseg);
   else
-    launch_gemm_mode<GM_F64>(qsteps, count, sm, s, x, go, gt, mmax, nb);
+    launch_gemm_mode<GM_F64>(qsteps, count, sm, s, x, go, gt, mmax, nb, segs, nseg);
 }
 
 // tpw = tiles per warp of the stage's largest output tile
 template <int S>
 static void launch_gemm_tc(int tpw, int count, size_t sm, cudaStream_t s, const ExecCtx* x, const GemmOut* go,
-                           const GemmTerm* gt, int mmax, int nb) {
+                           const GemmTerm* gt, int mmax, int nb, const BatchSeg* segs, int nseg) {
   if (tpw <= 1)
-    k_gemm_tc<S, 1><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+    k_gemm_tc<S, 1><<<count, 256, sm, s>>>(x, go, gt, mmax, nb, segs, nseg);
   else if (tpw <= 2)
-    k_gemm_tc<S, 2><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+    k_gemm_tc<S, 2><<<count, 256, sm, s>>>(x, go, gt, mmax, nb, segs, nseg);
   else
-    k_gemm_tc<S, 4><<<count, 256, sm, s>>>(x, go, gt, mmax, nb);
+    k_gemm_tc<S, 4><<<count, 256, sm, s>>>(x, go, gt, mmax, nb, segs, nseg);
 }
 
 int stage_launches(const Stage& st) {
   return (st.kind == ST_SVD && st.smem > 8 * SVD_SMALL_DOUBLES) ? 2 : 1;
 }
 
-void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaStream_t s) {
-  if (st.count <= 0) return;
+GemmShape gemm_shape(int aux) {
+  GemmShape g;
+  const int shape = aux & ~GEMM_AUX_FLAGS;
+  g.mmax = shape ? ((shape >> 16) & 0xff) : GT;
+  g.nb = shape ? (shape & 0xffff) : GT;
+  g.slices = (aux & GEMM_AUX_TC7) ? 7 : (aux & GEMM_AUX_TC5) ? 5 : 0;
+  g.mode = (aux & GEMM_AUX_DF) ? GM_DF : (aux & GEMM_AUX_FP32) ? GM_F32 : GM_F64;
+  if (g.slices) {
+    const int tiles = ((g.mmax + 15) / 16) * ((g.nb + 7) / 8);
+    g.variant = (tiles + 7) / 8;                 // tiles per warp
+    g.variant = g.variant <= 1 ? 1 : g.variant <= 2 ? 2 : 4;
+    g.smem = gemm_tc_smem_bytes(g.slices, g.mmax, g.nb);
+  } else {
+    const int rstep = 256 / g.nb;
+    const int qsteps = (g.mmax + rstep - 1) / rstep;  // outputs per thread
+    g.variant = qsteps <= 1 ? 1 : qsteps <= 4 ? 4 : GQ;
+    g.smem = (int)((g.mode == GM_F32 ? sizeof(float) : sizeof(double)) * gemm_smem_doubles(g.mmax, g.nb));
+  }
+  return g;
+}
+
+// A GEMM stage (x, j: one product; segs: a batched launch of `count` jobs).
+static void launch_gemm_stage(const GemmShape& g, int count, const ExecCtx* x, const GemmOut* go,
+                              const GemmTerm* gt, const BatchSeg* segs, int nseg, cudaStream_t s) {
+  if (g.slices == 7)
+    launch_gemm_tc<7>(g.variant, count, g.smem, s, x, go, gt, g.mmax, g.nb, segs, nseg);
+  else if (g.slices == 5)
+    launch_gemm_tc<5>(g.variant, count, g.smem, s, x, go, gt, g.mmax, g.nb, segs, nseg);
+  else
+    launch_gemm(g.mode, g.variant, count, g.smem, s, x, go, gt, g.mmax, g.nb, segs, nseg);
+}
+
+static void launch_kind(const Stage& st, int count, const ExecCtx* x, const DeviceJobs& j, const BatchSeg* segs,
+                        int nseg, cudaStream_t s) {
   switch (st.kind) {
     case ST_GEMM:
-    {
-      const int shape = st.aux & ~GEMM_AUX_FLAGS;
-      const int mmax = shape ? ((shape >> 16) & 0xff) : GT, nb = shape ? (shape & 0xffff) : GT;
-      if (st.aux & (GEMM_AUX_TC5 | GEMM_AUX_TC7)) {
-        const int tiles = ((mmax + 15) / 16) * ((nb + 7) / 8), tpw = (tiles + 7) / 8;
-        const GemmOut* go = j.gemm_out + st.first;
-        if (st.aux & GEMM_AUX_TC7)
-          launch_gemm_tc<7>(tpw, st.count, gemm_tc_smem_bytes(7, mmax, nb), s, x, go, j.gemm_term, mmax, nb);
-        else
-          launch_gemm_tc<5>(tpw, st.count, gemm_tc_smem_bytes(5, mmax, nb), s, x, go, j.gemm_term, mmax, nb);
-        break;
-      }
-      const int mode = (st.aux & GEMM_AUX_DF) ? GM_DF : (st.aux & GEMM_AUX_FP32) ? GM_F32 : GM_F64;
-      const size_t sm = (mode == GM_F32 ? sizeof(float) : sizeof(double)) * gemm_smem_doubles(mmax, nb);
-      const int rstep = 256 / nb;
-      const GemmOut* go = j.gemm_out + st.first;
-      launch_gemm(mode, (mmax + rstep - 1) / rstep, st.count, sm, s, x, go, j.gemm_term, mmax, nb);
-    }
+      launch_gemm_stage(gemm_shape(st.aux), count, x, segs ? nullptr : j.gemm_out + st.first, j.gemm_term, segs,
+                        nseg, s);
       break;
     case ST_COPY:
-      k_copy<<<st.count, 256, 0, s>>>(x, j.copy + st.first);
+      k_copy<<<count, 256, 0, s>>>(x, segs ? nullptr : j.copy + st.first, segs, nseg);
       break;
     case ST_QR:
-      k_qr<<<st.count, 256, st.smem, s>>>(x, j.qr + st.first, st.smem / 8);
+      k_qr<<<count, 256, st.smem, s>>>(x, segs ? nullptr : j.qr + st.first, st.smem / 8, segs, nseg);
       break;
     case ST_QAPPLY:
-      k_qapply<<<st.count, 256, 0, s>>>(x, j.qapply + st.first);
+      k_qapply<<<count, 256, 0, s>>>(x, segs ? nullptr : j.qapply + st.first, segs, nseg);
       break;
     case ST_SVD:
       {
@@ -1872,28 +2049,87 @@ void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaSt
       // per-column arrays of any job and the matrices that fit
       const int cmax = st.aux > 0 ? st.aux : SVD_MAXDIM;
       const size_t sm = st.smem > 0 ? (size_t)st.smem : 8 * (size_t)SVD_SMEM_DOUBLES;
+      const SvdJob* jobs = segs ? nullptr : j.svd + st.first;
       if (stage_launches(st) == 2) {
         // jobs that fit SVD_SMALL_DOUBLES in 128-thread CTAs (five per SM),
         // the rest in the stage's full-size CTAs
-        k_svd<<<st.count, 128, 8 * (size_t)SVD_SMALL_DOUBLES, s>>>(x, j.svd + st.first, st.first, SVD_SMALL_DOUBLES,
-                                                                   cmax, -1, SVD_SMALL_DOUBLES);
-        k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first, (int)(sm / 8), cmax, SVD_SMALL_DOUBLES,
-                                        INT_MAX);
+        k_svd<<<count, 128, 8 * (size_t)SVD_SMALL_DOUBLES, s>>>(x, jobs, st.first, SVD_SMALL_DOUBLES, cmax, -1,
+                                                                SVD_SMALL_DOUBLES, segs, nseg);
+        k_svd<<<count, 256, sm, s>>>(x, jobs, st.first, (int)(sm / 8), cmax, SVD_SMALL_DOUBLES, INT_MAX, segs, nseg);
       } else {
-        k_svd<<<st.count, 256, sm, s>>>(x, j.svd + st.first, st.first, (int)(sm / 8), cmax, -1, INT_MAX);
+        k_svd<<<count, 256, sm, s>>>(x, jobs, st.first, (int)(sm / 8), cmax, -1, INT_MAX, segs, nseg);
       }
     }
       break;
     case ST_NORM:
     {
       const int nmax = st.aux > 0 ? st.aux : NORM_MAXN;
-      k_norm<<<st.count, 256, norm_smem_bytes(nmax), s>>>(x, j.norm + st.first, nmax);
+      k_norm<<<count, 256, norm_smem_bytes(nmax), s>>>(x, segs ? nullptr : j.norm + st.first, nmax, segs, nseg);
     }
       break;
     case ST_SCAN:
-      k_scan<<<(st.count + 127) / 128, 128, 0, s>>>(x, j.scan + st.first, st.count);
+      k_scan<<<(count + 127) / 128, 128, 0, s>>>(x, j.scan + st.first, count);
       break;
   }
+}
+
+void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaStream_t s) {
+  if (st.count <= 0) return;
+  launch_kind(st, st.count, x, j, nullptr, 0, s);
+}
+
+void launch_stage_batched(const Stage& st, const BatchSeg* segs, int nseg, int total, cudaStream_t s) {
+  if (total <= 0 || st.kind == ST_SCAN) return;  // scans are launched per product
+  DeviceJobs none{};
+  launch_kind(st, total, nullptr, none, segs, nseg, s);
+}
+
+void launch_gemm_batched(const GemmShape& g, const BatchSeg* segs, int nseg, int total, cudaStream_t s) {
+  if (total > 0) launch_gemm_stage(g, total, nullptr, nullptr, nullptr, segs, nseg, s);
+}
+
+int gemm_chain_blocks_per_sm(const GemmShape& g) {
+  int nb = 0;
+  cudaError_t e = cudaSuccess;
+  if (g.slices == 7) {
+    if (g.variant <= 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_tc_chain<7, 1>, 256, g.smem);
+    else if (g.variant <= 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_tc_chain<7, 2>, 256, g.smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_tc_chain<7, 4>, 256, g.smem);
+  } else if (g.slices == 5) {
+    if (g.variant <= 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_tc_chain<5, 1>, 256, g.smem);
+    else if (g.variant <= 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_tc_chain<5, 2>, 256, g.smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_tc_chain<5, 4>, 256, g.smem);
+  } else {
+#define H2_OCC(Q, M) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm_chain<Q, M>, 256, g.smem)
+    if (g.mode == GM_DF) {
+      if (g.variant == 1) H2_OCC(1, GM_DF); else if (g.variant == 4) H2_OCC(4, GM_DF); else H2_OCC(GQ, GM_DF);
+    } else if (g.mode == GM_F32) {
+      if (g.variant == 1) H2_OCC(1, GM_F32); else if (g.variant == 4) H2_OCC(4, GM_F32); else H2_OCC(GQ, GM_F32);
+    } else {
+      if (g.variant == 1) H2_OCC(1, GM_F64); else if (g.variant == 4) H2_OCC(4, GM_F64); else H2_OCC(GQ, GM_F64);
+    }
+#undef H2_OCC
+  }
+  return e == cudaSuccess ? nb : 0;
+}
+
+void launch_gemm_chain(const GemmShape& g, int grid, const BatchSeg* segs, int nseg, int total, int* ctr,
+                       cudaStream_t s) {
+#define H2_CH(Q, M) k_gemm_chain<Q, M><<<grid, 256, g.smem, s>>>(segs, nseg, total, ctr, g.mmax, g.nb)
+#define H2_TCH(S_, T) k_gemm_tc_chain<S_, T><<<grid, 256, g.smem, s>>>(segs, nseg, total, ctr, g.mmax, g.nb)
+  if (g.slices == 7) {
+    if (g.variant <= 1) H2_TCH(7, 1); else if (g.variant <= 2) H2_TCH(7, 2); else H2_TCH(7, 4);
+  } else if (g.slices == 5) {
+    if (g.variant <= 1) H2_TCH(5, 1); else if (g.variant <= 2) H2_TCH(5, 2); else H2_TCH(5, 4);
+  } else if (g.mode == GM_DF) {
+    if (g.variant == 1) H2_CH(1, GM_DF); else if (g.variant == 4) H2_CH(4, GM_DF); else H2_CH(GQ, GM_DF);
+  } else if (g.mode == GM_F32) {
+    if (g.variant == 1) H2_CH(1, GM_F32); else if (g.variant == 4) H2_CH(4, GM_F32); else H2_CH(GQ, GM_F32);
+  } else {
+    if (g.variant == 1) H2_CH(1, GM_F64); else if (g.variant == 4) H2_CH(4, GM_F64); else H2_CH(GQ, GM_F64);
+  }
+#undef H2_CH
+#undef H2_TCH
 }
 
 }  // namespace h2

@@ -48,11 +48,29 @@ struct DeviceJobs {
   const NormJob* norm = nullptr;
 };
 
+// Launch parameters of a GEMM stage from its Stage::aux: largest tile,
+// compute mode, slices (tensor-core forms), kernel variant (outputs per thread
+// or tiles per warp) and dynamic shared memory.
+struct GemmShape {
+  int mmax, nb, mode, slices, variant, smem;
+};
+GemmShape gemm_shape(int aux);
+
 cudaError_t kernels_init();
 size_t gemm_smem_bytes();
 // kernel launches of a stage (an SVD stage of mixed job sizes takes two)
 int stage_launches(const Stage& st);
 void launch_stage(const Stage& st, const ExecCtx* x, const DeviceJobs& j, cudaStream_t s);
+// One launch of stage kind/shape st over `total` jobs of several products
+// (segments in device memory, sorted by start); scans are not batched.
+void launch_stage_batched(const Stage& st, const BatchSeg* segs, int nseg, int total, cudaStream_t s);
+// Persistent launch of a chain of GEMM stages: `grid` CTAs (at most the
+// resident ones) take the `total` jobs from the queue ctr[0] (zeroed
+// beforehand with the done counters).
+void launch_gemm_batched(const GemmShape& g, const BatchSeg* segs, int nseg, int total, cudaStream_t s);
+int gemm_chain_blocks_per_sm(const GemmShape& g);
+void launch_gemm_chain(const GemmShape& g, int grid, const BatchSeg* segs, int nseg, int total, int* ctr,
+                       cudaStream_t s);
 void launch_finalize(const ExecCtx* x, int nrank, cudaStream_t s);
 
 }  // namespace h2

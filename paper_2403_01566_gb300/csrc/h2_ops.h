@@ -192,4 +192,21 @@ struct ExecCtx {
   int* svd_sweeps;  // per SVD job: sweeps executed (profiling)
 };
 
+// A segment of a batched launch (one launch over the jobs of several
+// products): blocks / queue indices [start, start + count) run the jobs
+// jobs[0 .. count) of the product whose control block is ctx.  In a chained
+// GEMM launch (consecutive GEMM stages of many products in one persistent
+// kernel fed by a work queue) a job first waits until counter wait_idx
+// reaches wait_target (its product's previous stage is complete; -1: no
+// wait) and, when done, increments counter done_idx (-1: none).  first = the
+// segment's first job index in the product's job arrays.
+struct BatchSeg {
+  const ExecCtx* ctx;
+  const void* jobs;
+  const GemmTerm* terms;
+  int start, count;
+  int wait_idx, wait_target, done_idx;
+  int first;
+};
+
 }  // namespace h2

@@ -29,6 +29,10 @@ class MulOpts(C.Structure):
                 ("stream", C.c_void_p), ("svd_max_sweeps", C.c_int)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("test_unreachable_wait", C.c_int)]
+
+
 class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("dim", C.c_int), ("depth", C.c_int), ("nclusters", C.c_int),
                 ("nadm", C.c_int), ("ninadm", C.c_int), ("kpad", C.c_int), ("row_rank_min", C.c_int),
@@ -77,6 +81,15 @@ def _lib():
         lib.h2_server_wait.argtypes = [vp, i64, C.POINTER(vp), C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.h2_server_destroy.argtypes = [vp]
         lib.h2_server_destroy.restype = None
+        lib.h2_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), dp, C.POINTER(MulOpts),
+                                        C.POINTER(BatchOpts), C.POINTER(vp)]
+        lib.h2_batch_run.argtypes = [vp, vp, C.c_int]
+        lib.h2_batch_result.argtypes = [vp, C.c_int, C.POINTER(vp)]
+        lib.h2_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        lib.h2_batch_autotune.argtypes = [vp, C.POINTER(C.c_int)]
+        lib.h2_tuning_table.argtypes = [C.c_char_p, C.c_int]
+        lib.h2_batch_free.argtypes = [vp]
+        lib.h2_batch_free.restype = None
         lib.h2_to_dense.argtypes = [vp, vp, C.c_int]
         lib.h2_info.argtypes = [vp, C.POINTER(Stats)]
         lib.h2_ranks.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -97,10 +110,12 @@ def _check(rc, where):
 
 
 class H2Matrix:
-    """Owning wrapper of an h2_matrix handle."""
+    """Wrapper of an h2_matrix handle (owning unless owned=False: then the
+    handle belongs to a batch and is never freed here)."""
 
-    def __init__(self, handle):
+    def __init__(self, handle, owned=True):
         self._h = C.c_void_p(handle)
+        self._owned = owned
 
     @property
     def handle(self):
@@ -108,7 +123,8 @@ class H2Matrix:
 
     def free(self):
         if self._h and self._h.value:
-            _lib().h2_free(self._h)
+            if self._owned:
+                _lib().h2_free(self._h)
             self._h = C.c_void_p(0)
 
     def __del__(self):
@@ -314,3 +330,60 @@ def exported_symbols():
     import re
     text = open(HEADER).read()
     return sorted(set(re.findall(r"\b(h2_[a-z_]+)\s*\(", text)))
+
+
+class Batch:
+    """Many products in merged launches (h2_batch_*): Batch([(A, B, eps), ...])
+    plans them, run() replays the captured batch, result(i) is the i-th
+    product (owned by the batch, overwritten by the next run)."""
+
+    def __init__(self, products, precision=0, max_rank=0, test_unreachable_wait=False):
+        self._ops = [(a, b) for a, b, _ in products]  # operands stay alive with the batch
+        n = len(products)
+        A = (C.c_void_p * n)(*[a.handle.value for a, _, _ in products])
+        B = (C.c_void_p * n)(*[b.handle.value for _, b, _ in products])
+        eps = (C.c_double * n)(*[float(e) for _, _, e in products])
+        o = MulOpts()
+        o.theta, o.max_rank, o.precision, o.sync = 0.0, int(max_rank), int(precision), 1
+        bo = BatchOpts()
+        bo.test_unreachable_wait = 1 if test_unreachable_wait else 0
+        h = C.c_void_p()
+        _check(_lib().h2_batch_create(n, A, B, eps, C.byref(o), C.byref(bo), C.byref(h)), "h2_batch_create")
+        self._h = h
+        self.n = n
+
+    def run(self, sync=True, stream=None):
+        _check(_lib().h2_batch_run(self._h, C.c_void_p(stream) if stream else None, 1 if sync else 0), "h2_batch_run")
+
+    def result(self, i) -> H2Matrix:
+        h = C.c_void_p()
+        _check(_lib().h2_batch_result(self._h, int(i), C.byref(h)), "h2_batch_result")
+        return H2Matrix(h.value, owned=False)
+
+    def info(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(_lib().h2_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c)), "h2_batch_info")
+        return {"launches": a.value, "chains": b.value, "kernel_launches": c.value}
+
+    def autotune(self):
+        n = C.c_int()
+        _check(_lib().h2_batch_autotune(self._h, C.byref(n)), "h2_batch_autotune")
+        return n.value
+
+    def free(self):
+        if self._h and self._h.value:
+            _lib().h2_batch_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def tuning_table() -> str:
+    n = _lib().h2_tuning_table(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    _lib().h2_tuning_table(buf, n + 1)
+    return buf.value.decode()
