@@ -3,9 +3,12 @@
 Workload (one step = one product C = A*B through h2_mul, inputs resident in
 HBM): 128 x 128 grid on the unit square (n = 16384), A = -log|x-y|/(2 pi)
 (diagonal 1), B = exp(-|x-y|^2/0.1), leaf size 64, eta 2, tensor Chebyshev
-order 4 (k = 16).  `value` is the plain FP64 form timed with CUDA events;
-`chosen_form` is the served, mixed-precision form (continuous batching over
-streams with compensated contractions), timed beside it.
+order 4 (k = 16).  `value` is the chosen form: the products run as batches
+(h2_batch: merged launches and persistent GEMM chains, one CUDA graph replay
+per batch) with the tensor-core contractions (precision 4), timed with CUDA
+events around the replays; `plain_fp64` is h2_mul one product per step in
+FP64, timed the same way; the served form and a request stream shaped like
+the serving workload are reported beside them.
 
 Roofline: the algorithmic work of one product is the one counted by the CPU
 oracle's counters (tests/golden/work_counts.json, written from the oracle
@@ -44,7 +47,7 @@ def workload_config(grid=GRID):
     return {
         "workload": f"grid2d_n{grid * grid}: C=A*B, A=-log|x-y|/(2pi) diag 1, B=exp(-|x-y|^2/0.1), "
                     f"leaf 64, eta 2, Chebyshev order 4 (k=16), eps={EPS:g}",
-        "n": grid * grid, "k": 16, "leaf_size": 64, "eta": 2.0, "eps": EPS, "form": "plain FP64",
+        "n": grid * grid, "k": 16, "leaf_size": 64, "eta": 2.0, "eps": EPS,
         "l2": "flushed between timed steps (256 MiB write)",
     }
 
@@ -188,7 +191,7 @@ def run_reference(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": nprod,
         "warmup": max(1, args.warmup), "ms_per_step": 1e3 * sum(ts) / nprod, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": workload_config(),
+        "config": dict(workload_config(), parallelism=f"replicas x{world}"), "form": "CPU oracle, FP64",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{nprod} full product(s) of the workload on one host thread "
                                    f"(numpy FP64 oracle, input build excluded; at most {args.steps} steps, "
@@ -198,6 +201,74 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_size_for(steps, cap=24):
+    """Largest divisor of `steps` not above `cap`: products per batch replay
+    (every product of a batch holds its own workspace)."""
+    for b in range(min(cap, steps), 0, -1):
+        if steps % b == 0:
+            return b
+    return 1
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
+def serving_stream(h2, I, np, torch, nreq=48, rate=200.0, nmax=16384, seed=20240308):
+    """Requests shaped like the serving workload, scaled to one GPU: Poisson
+    arrivals at `rate` per second of products over a resident pool of 3D
+    uniform point sets (n log-uniform in [4096, nmax], k = 64, both kernels
+    1/|x-y| and exp(-|x-y|)), eps per request drawn from {1e-4, 1e-6, 1e-8};
+    continuous batching on 8 streams with admission by device memory; latency
+    from arrival to completion."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for j in range(4):
+        n = int(round(math.exp(rng.uniform(math.log(4096), math.log(nmax)))))
+        pts = I.uniform_points(n, 3, 5000 + j)
+        pool.append((n, h2.build(pts, I.INV, 2.0, 64, 4), h2.build(pts, I.EXP, 2.0, 64, 4)))
+    reqs = []
+    t = 0.0
+    for _ in range(nreq):
+        t += rng.exponential(1.0 / rate)
+        n, a, b = pool[int(rng.integers(len(pool)))]
+        ka, kb = int(rng.integers(2)), int(rng.integers(2))
+        eps = float(rng.choice([1e-4, 1e-6, 1e-8]))
+        reqs.append((t, (a, b)[ka], (a, b)[kb], eps, n))
+    srv = h2.Server(slots=8)
+    for n, a, b in pool:  # plans and graphs of every structure before the stream
+        srv.wait(srv.submit(a, b, 1e-6, precision=4))[0].free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for (ta, A, B, eps, n) in reqs:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((srv.submit(A, B, eps, precision=4), ta))
+    lat = []
+    t_last = 0.0
+    refused = {}
+    for (tk, ta), r in zip(tickets, reqs):
+        try:
+            C, _, tot = srv.wait(tk)
+            C.free()
+            lat.append(tot)
+        except h2.H2Error as ex:  # e.g. ranks above the cap of 64 at eps = 1e-8
+            key = f"{h2._lib().h2_strerror(ex.code).decode()} (eps {r[3]:g})"
+            refused[key] = refused.get(key, 0) + 1
+        t_last = max(t_last, time.perf_counter() - t0)
+    srv.close()
+    return {"requests": nreq, "completed": len(lat), "refused": refused, "rate_per_s": rate,
+            "n_range": [min(r[4] for r in reqs), max(r[4] for r in reqs)],
+            "value": len(lat) / t_last, "unit": UNIT, "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
+            "form": "served (continuous batching, 8 streams, memory admission), tensor-core contractions",
+            "workload": f"3D uniform points, n log-uniform in [4096, {nmax}] (4 resident point sets), k=64, leaf 64, "
+                        "eta 2, A/B in {1/|x-y|, exp(-|x-y|)}, eps in {1e-4, 1e-6, 1e-8}, Poisson arrivals",
+            "timing": "host wall clock; latency = arrival to completion, throughput = requests / last completion"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,6 +276,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the served, stream and end-to-end measurements")
     ap.add_argument("--grid", type=int, default=GRID,
                     help="grid side (default 128 = the benchmark workload; smaller for profiler captures)")
     args = ap.parse_args()
@@ -238,96 +310,122 @@ def main():
     sptr = stream.cuda_stream
     assert sptr != 0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    warm = max(args.warmup, 3)
 
-    # warm-up (plan build, graph capture, pool growth)
-    for _ in range(max(args.warmup, 3)):
-        h2.mul(A, B, EPS, stream=sptr)
+    # ---- chosen form: the benchmark products as batches of the tensor-core
+    # precision form (7-slice BF16 on the 64 x 64 stages, compensated FP32 on
+    # the others; FP64 QR/SVD/norms), each batch one CUDA graph replay
+    bs = batch_size_for(args.steps)
+    batch = h2.Batch([(A, B, EPS)] * bs, precision=4)
+    for _ in range(warm):
+        batch.run(sync=False, stream=sptr)
     torch.cuda.synchronize()
-
-    # timed steps: device time per product with CUDA events on the product's stream
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    outs = []
+    nrep = args.steps // bs
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nrep)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nrep)]
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
     t_wall0 = time.perf_counter()
-    for i in range(args.steps):
+    for i in range(nrep):
         flush.fill_(float(i))
         starts[i].record(stream)
-        outs.append(h2.mul(A, B, EPS, sync=False, stream=sptr))
+        batch.run(sync=False, stream=sptr)
         ends[i].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
     if dist is not None:
         dist.barrier()
+    batch.run(sync=True, stream=sptr)  # device error state of the products
+    rep_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+    total_ms = max_over_ranks(sum(rep_ms), dist, "cuda")
+    value = whole_job_rate(world, args.steps, total_ms)
+    binfo = batch.info()
+    launches = binfo["kernel_launches"] * nrep
+    st_c = batch.result(0).info()
+    y_chk = batch.result(0).matvec(I.random_vector(w.n, 3))
+    batch.free()
+
+    # ---- plain FP64 form: one product per step through h2_mul
+    for _ in range(warm):
+        h2.mul(A, B, EPS, stream=sptr)
+    torch.cuda.synchronize()
+    p_st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    p_en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    outs = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        p_st[i].record(stream)
+        outs.append(h2.mul(A, B, EPS, sync=False, stream=sptr))
+        p_en[i].record(stream)
+    torch.cuda.synchronize()
     for C in outs:
         C.check()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
-    value = whole_job_rate(world, args.steps, total_ms)
-    launches = outs[0].info().launches * args.steps
+    y_ref = outs[0].matvec(I.random_vector(w.n, 3))
     st0 = outs[0].info()
     for C in outs:
         C.free()
     outs.clear()
+    plain_ms = [s_.elapsed_time(e_) for s_, e_ in zip(p_st, p_en)]
+    plain_total = max_over_ranks(sum(plain_ms), dist, "cuda")
+    plain_value = whole_job_rate(world, args.steps, plain_total)
+    agree = float(np.linalg.norm(y_chk - y_ref) / np.linalg.norm(y_ref))
 
-    # the served form (continuous batching, h2_server_*): `steps` products of
-    # the same workload submitted at once over the resident operands; wall
-    # time from the first submission to the last completion
-    served = None
-    if True:  # every rank serves on its own GPU; rank 0 reports
+    served = stream_run = None
+    e2e_value = None
+    x = np.ascontiguousarray(I.random_vector(w.n, 1))
+    pts_pinned = torch.from_numpy(np.ascontiguousarray(w.points)).pin_memory()
+    if not args.no_extras:
+        # served form: `steps` products submitted at once (continuous batching)
         slots = 4
         srv = h2.Server(slots=slots)
-        for t in [srv.submit(A, B, EPS, precision=2) for _ in range(slots)]:  # plan instances, graphs
+        for t in [srv.submit(A, B, EPS, precision=4) for _ in range(slots)]:
             srv.wait(t)[0].free()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tickets = [srv.submit(A, B, EPS, precision=2) for _ in range(args.steps)]
+        tickets = [srv.submit(A, B, EPS, precision=4) for _ in range(args.steps)]
         lat = []
         for t in tickets:
             Cs, _, tot = srv.wait(t)
             lat.append(tot)
             Cs.free()
-        torch.cuda.synchronize()
         el = time.perf_counter() - t0
         srv.close()
-        lat.sort()
-        served = {"form": f"served and mixed precision: continuous batching on {slots} streams, compensated FP32 "
-                          "contractions (~1e-13), FP64 QR/SVD/rank decisions/norms",
-                  "value": args.steps / el, "unit": UNIT, "vs_plain_fp64": (args.steps / el) / value,
-                  "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+        served = {"form": f"served: continuous batching on {slots} streams, tensor-core contractions",
+                  "value": args.steps / el, "unit": UNIT, "p50_ms": percentile(lat, 0.5),
+                  "p99_ms": percentile(lat, 0.99),
                   "timing": f"host wall clock over {args.steps} products submitted at once (latency = submit to done)"}
+        # end to end through the public API: points from pinned host memory ->
+        # h2_build (A, B) -> h2_mul (tensor-core form) -> C x read back, per step
+        e2e_steps = max(2, min(5, args.steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            p = pts_pinned.numpy()
+            Ae = h2.build(p, w.kernel_a, w.eta, w.leaf_size, w.order)
+            Be = h2.build(p, w.kernel_b, w.eta, w.leaf_size, w.order)
+            Ce = h2.mul(Ae, Be, EPS, stream=sptr, precision=4)
+            y = Ce.matvec(x)
+            Ce.free()
+            Ae.free()
+            Be.free()
+        torch.cuda.synchronize()
+        e2e_value = e2e_steps / (time.perf_counter() - t0)
+        assert np.isfinite(y).all()
+        # last: the stream's structures take the places of the plan cache
+        if rank == 0:
+            stream_run = serving_stream(h2, I, np, torch)
 
-    # end to end through the public API: points from pinned host memory ->
-    # h2_build (A, B) -> h2_mul -> C x read back to the host, per step.
-    pts_pinned = torch.from_numpy(np.ascontiguousarray(w.points)).pin_memory()
-    x = np.ascontiguousarray(I.random_vector(w.n, 1))
-    e2e_steps = max(2, min(5, args.steps))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        p = pts_pinned.numpy()
-        Ae = h2.build(p, w.kernel_a, w.eta, w.leaf_size, w.order)
-        Be = h2.build(p, w.kernel_b, w.eta, w.leaf_size, w.order)
-        Ce = h2.mul(Ae, Be, EPS, stream=sptr)
-        y = Ce.matvec(x)
-        Ce.free()
-        Ae.free()
-        Be.free()
-    torch.cuda.synchronize()
-    e2e_value = e2e_steps / (time.perf_counter() - t0)
-    assert np.isfinite(y).all()
-
-    # roofline of the dominant kernel: one profiled product (stages one by one)
+    # roofline of the dominant kernel of the chosen form: one profiled product
+    # (stages one by one, CUDA events around each)
     prof = (h2.KernelProf * len(KIND_NAMES))()
-    Cp = h2.mul_profile(A, B, EPS, prof, stream=sptr)
+    Cp = h2.mul_profile(A, B, EPS, prof, stream=sptr, precision=4)
     Cp.free()
     kinds = [(KIND_NAMES[i], prof[i]) for i in range(len(KIND_NAMES))]
-    prof_total = sum(p.ms for _, p in kinds)
+    prof_total = sum(p_.ms for _, p_ in kinds)
     dom_name, dom = max(kinds, key=lambda kv: kv[1].ms)
     peak = fp64_peak()
     executed = dom.flops / (dom.ms / 1e3) / 1e12 if dom.ms > 0 else 0.0
@@ -356,18 +454,27 @@ def main():
                          "input build excluded)"}
 
     if rank == 0:
-        pcts = sorted(step_ms)
-        p50 = statistics.median(pcts)
-        p99 = pcts[min(len(pcts) - 1, int(math.ceil(0.99 * len(pcts))) - 1)]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(grid), parallelism=f"replicas x{world}"),
-            "p50_ms": p50, "p99_ms": p99, "wall_s": t_wall,
+            "form": "chosen: batched products, tensor-core contractions",
+            "chosen_form": {"form": f"batched: {bs} products per CUDA-graph replay (merged launches, persistent GEMM "
+                                    "chains), 7-slice BF16 tensor-core GEMMs on 64x64 stages and compensated FP32 "
+                                    "on the others, FP64 QR/SVD/rank decisions/norms",
+                            "products_per_batch": bs, "replays": nrep,
+                            "p50_ms_per_batch": percentile(rep_ms, 0.5), "p99_ms_per_batch": percentile(rep_ms, 0.99),
+                            "vs_plain_fp64": value / plain_value, "Cx_rel_diff_vs_plain_fp64": agree,
+                            "launches_per_batch": binfo},
+            "plain_fp64": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_total / args.steps,
+                           "p50_ms": percentile(plain_ms, 0.5), "p99_ms": percentile(plain_ms, 0.99),
+                           "form": "h2_mul one product per step, FP64 throughout"},
+            "p50_ms": percentile(rep_ms, 0.5) / bs, "p99_ms": percentile(rep_ms, 0.99) / bs, "wall_s": t_wall,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * w.points.nbytes + x.nbytes), "d2h_bytes_per_step": int(x.nbytes),
-                    "what": "h2_build(A), h2_build(B) from pinned host points, h2_mul, C x read back"},
+                    "what": "h2_build(A), h2_build(B) from pinned host points, h2_mul (tensor-core form), "
+                            "C x read back"} if e2e_value else None,
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
@@ -378,13 +485,14 @@ def main():
                          "work_source": "oracle counters, tests/golden/work_counts.json" if method_flops
                          else "kernel counts (no oracle count recorded for this workload)",
                          "peak_source": "FP64 ALU peak derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                         "profiled_form": "tensor-core form (precision 4), stages one by one",
                          "share": dom.ms / prof_total if prof_total else None,
                          "executed": {"achieved": executed, "frac": executed / peak if peak else None,
                                       "gpu_flops_per_product": dom.flops,
                                       "method_flops_per_product": method_flops,
                                       "gpu_over_method": dom.flops / method_flops if method_flops else None},
                          "product": {"method_gflop": sum(mw["flops"].values()) / 1e9 if mw else None,
-                                     "gpu_gflop": sum(p.flops for _, p in kinds) / 1e9,
+                                     "gpu_gflop": sum(p_.flops for _, p_ in kinds) / 1e9,
                                      "method_tflops_over_product_time":
                                          sum(mw["flops"].values()) / (prof_total / 1e3) / 1e12 if mw else None},
                          "hbm_copy": {"kernel": "k_copy", "gb": kc.bytes / 1e9, "ms": kc.ms,
@@ -392,12 +500,14 @@ def main():
                                       "peak_gbs": hbm_peak,
                                       "frac": (kc.bytes / (kc.ms / 1e3) / 1e9) / hbm_peak
                                       if (kc.ms > 0 and hbm_peak) else None} if kc else None},
-            "kernels": {nm: {"launches": p.launches, "jobs": p.jobs, "ms": round(p.ms, 4),
-                             "gflop": round(p.flops / 1e9, 4), "gb": round(p.bytes / 1e9, 4)} for nm, p in kinds},
+            "kernels": {nm: {"launches": p_.launches, "jobs": p_.jobs, "ms": round(p_.ms, 4),
+                             "gflop": round(p_.flops / 1e9, 4), "gb": round(p_.bytes / 1e9, 4)} for nm, p_ in kinds},
             "product": {"nadm": st0.nadm, "ninadm": st0.ninadm, "agglomerated": st0.nagglomerated,
-                        "rank_max": max(st0.row_rank_max, st0.col_rank_max), "workspace_gb": st0.workspace_bytes / 1e9},
+                        "rank_max": max(st0.row_rank_max, st0.col_rank_max), "workspace_gb": st0.workspace_bytes / 1e9,
+                        "rank_max_chosen": max(st_c.row_rank_max, st_c.col_rank_max)},
             "clocks": clocks,
-            "chosen_form": served,
+            "served_form": served,
+            "serving_stream": stream_run,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
