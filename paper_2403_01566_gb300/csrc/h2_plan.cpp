@@ -29,6 +29,7 @@
 #include "h2_plan.h"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <functional>
 #include <stdexcept>
@@ -97,6 +98,134 @@ inline Dim merged_width(const DimV& a, const DimV& b) {
   return Dim{a.c + b.c, -1, -1};
 }
 
+// Bits of a planning-time workspace offset that address the inside of a
+// buffer (up to 2^36 doubles); the bits above hold the buffer index.
+constexpr int WS_LOCAL_BITS = 36;
+constexpr int64_t WS_LOCAL_MASK = (int64_t(1) << WS_LOCAL_BITS) - 1;
+
+// Places the tagged workspace buffers of a finished product plan by lifetime
+// and rewrites every workspace pointer of its jobs; returns the workspace
+// length (doubles).  A buffer lives from the first to the last stage whose
+// jobs address it; buffers of the same lifetime are laid out as one group,
+// and the groups are placed first-fit in order of first use, a group's space
+// being free again from the stage after its last use.  Stages of one product
+// run in order (a chained GEMM stage waits for its product's previous one),
+// so two buffers share memory only when no stage can see both.  The
+// arithmetic of every job is unchanged: only addresses move.
+static int64_t pack_workspace(Plan& P, const std::vector<int64_t>& bufs) {
+  const size_t nb = bufs.size();
+  std::vector<int> first(nb, INT_MAX), last(nb, -1);
+  auto touch = [&](const Ptr& p, int s) {
+    if (p.arena != AR_WS) return;
+    const size_t id = (size_t)(p.off >> WS_LOCAL_BITS);
+    if (id >= nb) throw std::runtime_error("workspace pointer outside every buffer");
+    first[id] = std::min(first[id], s);
+    last[id] = std::max(last[id], s);
+  };
+  auto each_ptr = [&](auto&& f) {
+    for (size_t si = 0; si < P.stages.size(); ++si) {
+      const Stage& st = P.stages[si];
+      const int s = (int)si;
+      for (int j = 0; j < st.count; ++j) {
+        const int64_t J = st.first + j;
+        switch (st.kind) {
+          case ST_GEMM: {
+            GemmOut& O = P.gout[J];
+            f(O.o, s);
+            for (int t = O.t0; t < O.t1; ++t) {
+              GemmTerm& T = P.gterm[t];
+              f(T.a, s);
+              f(T.b, s);
+              f(T.c, s);
+            }
+            break;
+          }
+          case ST_COPY: f(P.copy[J].src, s); f(P.copy[J].dst, s); break;
+          case ST_QR: f(P.qr[J].a, s); f(P.qr[J].tau, s); f(P.qr[J].r, s); f(P.qr[J].piv, s); break;
+          case ST_QAPPLY: f(P.qap[J].a, s); f(P.qap[J].tau, s); f(P.qap[J].y, s); f(P.qap[J].out, s); break;
+          case ST_SVD: f(P.svd[J].src, s); f(P.svd[J].u, s); f(P.svd[J].sig, s); f(P.svd[J].piv, s); break;
+          case ST_NORM: f(P.norm[J].src, s); break;
+          default: break;
+        }
+      }
+    }
+  };
+  each_ptr([&](Ptr& p, int s) { touch(p, s); });
+  // groups of equal lifetime, in order of first use
+  std::map<std::pair<int, int>, int64_t> gsize;
+  for (size_t i = 0; i < nb; ++i)
+    if (last[i] >= 0) gsize[{first[i], last[i]}] += bufs[i];
+  std::map<std::pair<int, int>, int64_t> gbase;
+  std::map<int64_t, int64_t> freel;  // free extents below `top`: start -> length
+  std::vector<std::pair<int, std::pair<int, int>>> frees;  // (stage at which free, group)
+  int64_t top = 0;
+  auto release = [&](int64_t st, int64_t len) {
+    int64_t en = st + len;
+    auto it = freel.lower_bound(st);
+    if (it != freel.end() && it->first == en) {
+      en += it->second;
+      it = freel.erase(it);
+    }
+    if (it != freel.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == st) {
+        st = pv->first;
+        freel.erase(pv);
+      }
+    }
+    if (en == top) top = st;
+    else freel[st] = en - st;
+    // a free extent that now ends at top shrinks top
+    while (!freel.empty()) {
+      auto lastf = std::prev(freel.end());
+      if (lastf->first + lastf->second != top) break;
+      top = lastf->first;
+      freel.erase(lastf);
+    }
+  };
+  std::multimap<int, std::pair<int, int>> ends;  // last stage -> group
+  int64_t peak = 0;
+  for (const auto& [g, len] : gsize) {
+    const int s = g.first;
+    // free every group whose last use lies before stage s
+    while (!ends.empty() && ends.begin()->first < s) {
+      const auto gg = ends.begin()->second;
+      release(gbase[gg], gsize[gg]);
+      ends.erase(ends.begin());
+    }
+    int64_t got = -1;
+    for (auto it = freel.begin(); it != freel.end(); ++it)
+      if (it->second >= len) {
+        got = it->first;
+        const int64_t rem = it->second - len;
+        freel.erase(it);
+        if (rem) freel[got + len] = rem;
+        break;
+      }
+    if (got < 0) {
+      got = top;
+      top += len;
+    }
+    peak = std::max(peak, top);
+    gbase[g] = got;
+    ends.insert({g.second, g});
+  }
+  // buffer bases: consecutive inside their group
+  std::vector<int64_t> base(nb, 0);
+  std::map<std::pair<int, int>, int64_t> gnext = gbase;
+  for (size_t i = 0; i < nb; ++i)
+    if (last[i] >= 0) {
+      int64_t& nx = gnext[{first[i], last[i]}];
+      base[i] = nx;
+      nx += bufs[i];
+    }
+  each_ptr([&](Ptr& p, int) {
+    if (p.arena != AR_WS) return;
+    p.off = base[(size_t)(p.off >> WS_LOCAL_BITS)] + (p.off & WS_LOCAL_MASK);
+  });
+  return std::max<int64_t>(peak, 1);
+}
+
 struct Builder {
   Plan& P;
   int64_t ws = 0, ws_peak = 0;
@@ -118,9 +247,18 @@ struct Builder {
   bool df_contractions = false;    // precision form 2
   bool tc5_contractions = false;   // precision form 3 (tensor cores, 5 slices)
   bool tc7_contractions = false;   // precision form 4 (tensor cores, 7 slices, with compensated FP32)
+  // Workspace buffers of a product plan are placed by lifetime once the
+  // stage list is complete (pack_workspace): while planning, an offset
+  // carries its buffer's index above the low WS_LOCAL_BITS bits, which hold
+  // the offset inside the buffer.  ws / ws_peak count the bump-allocated
+  // doubles (statistics; the placement of helper plans).
+  bool tagged = false;
+  std::vector<int64_t> bufs;  // sizes (doubles) of the tagged buffers
   int64_t alloc(int64_t n) {
-    const int64_t o = ws;
-    ws += (std::max<int64_t>(n, 1) + 31) & ~int64_t(31);
+    const int64_t sz = (std::max<int64_t>(n, 1) + 31) & ~int64_t(31);
+    const int64_t o = tagged ? ((int64_t)bufs.size() << WS_LOCAL_BITS) : ws;
+    if (tagged) bufs.push_back(sz);
+    ws += sz;
     ws_peak = std::max(ws_peak, ws);
     return o;
   }
@@ -361,6 +499,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   auto plan = std::make_shared<Plan>();
   Plan& P = *plan;
   Builder B(P);
+  B.tagged = true;  // workspace placed by lifetime at the end (pack_workspace)
   B.fp32_contractions = opt.precision == 1;
   B.df_contractions = opt.precision == 2;
   B.tc5_contractions = opt.precision == 3;
@@ -1320,7 +1459,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       P.rank_row_slot.push_back(F.f.m.s >= 0 ? F.f.m.s : B.slot(F.f.m.c));
     }
     B.flush_copy(TAG_COUPLE);
-    P.ws_len = B.ws_peak;
+    P.stats["ws_bump_bytes"] = B.ws_peak * 8;
+    P.ws_len = pack_workspace(P, B.bufs);
     P.fac_len = B.fac;
     P.stats["final_adm"] = fin.size();
     P.stats["stages"] = P.stages.size();
@@ -1609,7 +1749,8 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   }
   B.flush_gemm(TAG_COUPLE);
 
-  P.ws_len = B.ws_peak;
+  P.stats["ws_bump_bytes"] = B.ws_peak * 8;
+  P.ws_len = pack_workspace(P, B.bufs);
   P.fac_len = B.fac;
   P.stats["final_adm"] = fin.size();
   P.stats["stages"] = P.stages.size();
