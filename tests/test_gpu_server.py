@@ -24,17 +24,38 @@ def _operands(w):
             h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order))
 
 
-def test_each_result_same_alone_and_in_the_mix():
+def _blockrel_to_exact(C, w, eps):
+    """Largest ||C_b - (AB)_b||_2 / ||(AB)_b||_2 over the blocks of the oracle's
+    block tree of the product, against the exact dense product."""
+    from oracle import h2oracle as O
+    from tests.oracle_cases import build_pair
+    X, Y = build_pair(w)
+    Z = X.dense() @ Y.dense()
+    Cd = C.to_dense()
+    tb = O.build_block_tree(X.rows, Y.cols, w.eta)
+    worst = 0.0
+    for b in O.block_leaves(tb):
+        ix = np.ix_(b.t.idx, b.s.idx)
+        nz = np.linalg.norm(Z[ix], 2) or 1.0
+        worst = max(worst, np.linalg.norm(Cd[ix] - Z[ix], 2) / nz)
+    return worst
+
+
+@pytest.mark.parametrize("precision", [0, 2, 4])
+def test_each_result_same_alone_and_in_the_mix(precision):
     ws = [(I.grid_2d(32), 1e-6), (I.grid_2d(64), 1e-4), (I.plain_1d(1024), 1e-6), (I.grid_2d(32), 1e-4),
           (I.cube_3d(1200, seed=11, leaf=40, order=2), 1e-4), (I.grid_2d(64), 1e-6)]
     ops = [_operands(w) for w, _ in ws]
-    alone = [h2.mul(A, B, eps).to_dense() for (A, B), (_, eps) in zip(ops, ws)]
+    alone = [h2.mul(A, B, eps, precision=precision).to_dense() for (A, B), (_, eps) in zip(ops, ws)]
     srv = h2.Server(slots=4)
-    tickets = [srv.submit(A, B, eps) for (A, B), (_, eps) in zip(ops, ws)]
-    for t, ref in zip(tickets, alone):
+    tickets = [srv.submit(A, B, eps, precision=precision) for (A, B), (_, eps) in zip(ops, ws)]
+    for i, (t, ref) in enumerate(zip(tickets, alone)):
         C, q, tot = srv.wait(t)
         assert tot >= q >= 0.0
         assert np.array_equal(C.to_dense(), ref)
+        if i < 3:  # the bound claimed above, against the exact product
+            w, eps = ws[i]
+            assert _blockrel_to_exact(C, w, eps) <= eps
     srv.close()
 
 
