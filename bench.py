@@ -63,6 +63,37 @@ def load_json(*parts):
 ORACLE_KIND = {"k_gemm": ("gemm",), "k_qr": ("qr",), "k_qapply": (), "k_svd": ("svd",), "k_norm": ("norm",)}
 
 
+def kernel_table(kinds, mw, peak, hbm_peak):
+    """Per kernel of the profiled product: launches, time, executed and
+    oracle-counted work, and the fraction of its roofline (FP64 ALU peak for
+    the arithmetic kernels, HBM copy bandwidth for k_copy).  k_gemm mixes
+    tensor-core and compensated-FP32 stages; its fraction is against the FP64
+    peak the plain form would be bound by."""
+    out = {}
+    for nm, p_ in kinds:
+        if p_.launches == 0:
+            continue
+        s = p_.ms / 1e3
+        row = {"launches": p_.launches, "jobs": p_.jobs, "ms": round(p_.ms, 4),
+               "gflop": round(p_.flops / 1e9, 4), "gb": round(p_.bytes / 1e9, 4)}
+        if p_.flops > 0 and s > 0:
+            row["tflops_executed"] = round(p_.flops / s / 1e12, 4)
+            if peak:
+                row["frac_executed"] = round(p_.flops / s / 1e12 / peak, 4)
+            keys = ORACLE_KIND.get(nm, ())
+            if mw and keys:
+                mf = sum(mw["flops"][k] for k in keys)
+                row["tflops_method"] = round(mf / s / 1e12, 4)
+                if peak:
+                    row["frac_method"] = round(mf / s / 1e12 / peak, 4)
+        elif p_.bytes > 0 and s > 0:
+            row["gbs"] = round(p_.bytes / s / 1e9, 1)
+            if hbm_peak:
+                row["frac_hbm"] = round(p_.bytes / s / 1e9 / hbm_peak, 4)
+        out[nm] = row
+    return out
+
+
 def method_work(grid, eps):
     """Oracle-counted work of one product of the workload (None if not recorded)."""
     wc = load_json("tests", "golden", "work_counts.json")
@@ -500,8 +531,7 @@ def main():
                                       "peak_gbs": hbm_peak,
                                       "frac": (kc.bytes / (kc.ms / 1e3) / 1e9) / hbm_peak
                                       if (kc.ms > 0 and hbm_peak) else None} if kc else None},
-            "kernels": {nm: {"launches": p_.launches, "jobs": p_.jobs, "ms": round(p_.ms, 4),
-                             "gflop": round(p_.flops / 1e9, 4), "gb": round(p_.bytes / 1e9, 4)} for nm, p_ in kinds},
+            "kernels": kernel_table(kinds, mw, peak, hbm_peak),
             "product": {"nadm": st0.nadm, "ninadm": st0.ninadm, "agglomerated": st0.nagglomerated,
                         "rank_max": max(st0.row_rank_max, st0.col_rank_max), "workspace_gb": st0.workspace_bytes / 1e9,
                         "rank_max_chosen": max(st_c.row_rank_max, st_c.col_rank_max)},
