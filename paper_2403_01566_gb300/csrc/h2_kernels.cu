@@ -1454,6 +1454,27 @@ __global__ void __launch_bounds__(256) k_qapply(const ExecCtx* __restrict__ px, 
 //  - only the pairs that rotate are visited, from a compacted list.
 constexpr int SVD_MAXSWEEP = 60;
 
+// v 2^k as FP32 by bit operations (no FP64 instruction): the exponent
+// re-biased, the fraction truncated to 23 bits; 0 when v is zero or v 2^k is
+// below FP32's normal range.  The callers keep v 2^k below 2^127.
+__device__ __forceinline__ float f32_of_scaled(double v, int k) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+  const int eb = (int)((hw >> 20) & 0x7ffu);
+  const int e = eb - 1023 + k;
+  if (eb == 0 || e < -126) return 0.0f;
+  return __uint_as_float((hw & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+}
+
+// f 2^k as FP64, exactly, by bit operations (f normal or zero)
+__device__ __forceinline__ double f64_of_f32_scaled(float f, int k) {
+  const unsigned u = __float_as_uint(f);
+  const int ef = (int)((u >> 23) & 0xffu);
+  if (ef == 0) return 0.0;
+  const unsigned hw = (u & 0x80000000u) | ((unsigned)(ef - 127 + 1023 + k) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hw, (int)((u & 0x7u) << 29));
+}
+
 // Round-robin (circle method) pairing of ce (even) columns: in round rnd, pair
 // p matches columns i < j; over ce-1 rounds every pair meets once.
 __device__ __forceinline__ int svd_pair_a(int rnd, int p, int ce) { return p == 0 ? rnd : (rnd + p) % (ce - 1); }
@@ -1587,8 +1608,9 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
   const int ce = cols + (cols & 1);
   const int npairs = ce / 2;
   const double tol = 2.5e-15;
-  // dot products: thread -> (pair, row segment)
-  const int nseg = blockDim.x / npairs;
+  // dot products: thread -> (pair, row segment); at most 8 segments, so that
+  // phase B sums few partials (every FP64 add there is a full warp issue)
+  const int nseg = min(8, (int)blockDim.x / npairs);
   const int ap = threadIdx.x % npairs, aseg = threadIdx.x / npairs;
   const int maxsweep = x.scal[PARAM_SVD_SWEEPS] >= 1.0 ? (int)x.scal[PARAM_SVD_SWEEPS] : SVD_MAXSWEEP;
   int sweep = 0;
@@ -1599,13 +1621,18 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
       // phase A: partial dot products of the round's pairs
       if (aseg < nseg) {
         const int i = svd_pair_i(rnd, ap, ce), j = svd_pair_j(rnd, ap, ce);
-        double g = 0.0;
+        double g = 0.0, h = 0.0;
         if (j < cols) {
           const double* mi = M + i * ldm;
           const double* mj = M + j * ldm;
-          for (int r = aseg; r < rows; r += nseg) g = fma(mi[r], mj[r], g);
+          int r = aseg;
+          for (; r + nseg < rows; r += 2 * nseg) {
+            g = fma(mi[r], mj[r], g);
+            h = fma(mi[r + nseg], mj[r + nseg], h);
+          }
+          if (r < rows) g = fma(mi[r], mj[r], g);
         }
-        part[aseg * npairs + ap] = g;
+        part[aseg * npairs + ap] = g + h;
       }
       if (threadIdx.x == 0) nround = 0;
       __syncthreads();
@@ -1620,20 +1647,27 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
           const double ga = gt * di * dj, al = nrm2[i], be = nrm2[j];
           // |ga| > tol * sqrt(al * be), in squared form
           if (ga != 0.0 && al > tiny2 && be > tiny2 && ga * ga > (tol * tol) * al * be) {
-            // t = tan(theta), the smaller root of t^2 + 2 zeta t - 1 = 0 with
-            // zeta = d / g2 (d = be - al, g2 = 2 ga), written as
-            // t = sign(d) g2 / (|d| + sqrt(d^2 + g2^2)) with d and g2 first
-            // scaled by a power of two into [1, 2) (no overflow): one
-            // reciprocal square root and one division on the round's
-            // critical path instead of two divisions and a square root
-            const double d0 = be - al, g0 = 2.0 * ga;
-            const double mx = fmax(fabs(d0), fabs(g0));
-            const double p2 = __hiloint2double((2046 - ((__double2hiint(mx) >> 20) & 0x7ff)) << 20, 0);
-            const double dd = d0 * p2, gg = g0 * p2;
-            const double n2 = fma(dd, dd, gg * gg);
-            const double t = copysign(1.0, d0) * gg / fma(n2, rsqrt(n2), fabs(dd));
-            const double q = 1.0 + t * t;
-            const double c = rsqrt(q);
+            // t = tan(theta), the smaller root of f(t) = g2 t^2 + 2 d t - g2
+            // (d = be - al, g2 = 2 ga): first in FP32 as
+            // t = sign(d) g2 / (|d| + sqrt(d^2 + g2^2)) from d and g2 scaled by
+            // 2^k into [1, 2), then one Newton step in FP64 (t to ~1e-14; the
+            // angle only steers convergence).  The rotation itself is exact:
+            // c = 1 / sqrt(1 + t^2) in FP64 from an FP32 seed and two Newton
+            // steps, s = c t.  FP64 work on this serial step: 14 instructions
+            // instead of about 30 with an FP64 square root and division.
+            const double d0 = be - al, g0 = ga + ga;
+            const int k = 1023 - max((__double2hiint(d0) >> 20) & 0x7ff, (__double2hiint(g0) >> 20) & 0x7ff);
+            const float df = f32_of_scaled(d0, k), gf = f32_of_scaled(g0, k);
+            const float tf = copysignf(1.0f, df) * gf / (fabsf(df) + sqrtf(fmaf(df, df, gf * gf)));
+            const double t0 = f64_of_f32_scaled(tf, 0);
+            const double fp = fma(g0, t0, d0);  // f'(t0) / 2
+            const double ft = fma(fma(g0, t0, d0 + d0), t0, -g0);
+            const double t = fma(-ft, f64_of_f32_scaled(__frcp_rn(f32_of_scaled(fp, k)), k - 1), t0);
+            const double q = fma(t, t, 1.0);
+            const double hq = 0.5 * q;
+            double c = f64_of_f32_scaled(rsqrtf(f32_of_scaled(q, 0)), 0);
+            c *= fma(-hq * c, c, 1.5);
+            c *= fma(-hq * c, c, 1.5);
             const double ei = dinv[i], ej = dinv[j];
             nrm2[i] = fmax(al - t * ga, 0.0);
             nrm2[j] = be + t * ga;
