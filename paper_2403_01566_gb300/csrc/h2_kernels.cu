@@ -989,7 +989,7 @@ __device__ int householder_cols_la(double* a, int lda, int rows, int cols, doubl
     } else if (t != 0.0) {
       const int len = rows - j - 1;
       int ts = 32;
-      while (ts > 1 && ts * 8 > len) ts >>= 1;
+      while (ts > 1 && ts * 16 > len) ts >>= 1;
       const int tid = threadIdx.x - 32, nteam = ((int)blockDim.x - 32) / ts, team = tid / ts, tl = tid % ts;
       for (int c0 = j + 2; c0 < cols; c0 += nteam) apply(j, t, c0 + team, tl, ts);
     }
@@ -1109,11 +1109,13 @@ __device__ int householder_cols(double* a, int lda, int rows, int cols, double* 
     }
     const double t = sh[0];
     if (t != 0.0) {
-      // trailing columns: teams of ts lanes per column (short columns use small
-      // teams so that the FP64 shuffle reduction stays short)
+      // trailing columns: teams of ts lanes per column, at least 16 rows per
+      // lane (the FP64 shuffle reduction of a team costs log2(ts) full warp
+      // issues per column; 8 rows per lane measured 2% slower, 32 rows 20%
+      // slower through idle teams)
       const int len = rows - j - 1;
       int ts = 32;
-      while (ts > 1 && ts * 8 > len) ts >>= 1;
+      while (ts > 1 && ts * 16 > len) ts >>= 1;
       const int nteam = blockDim.x / ts, team = threadIdx.x / ts, tl = threadIdx.x % ts;
       for (int c0 = j + 1; c0 < cols; c0 += nteam) {
         const int c = c0 + team;
@@ -1222,7 +1224,7 @@ __device__ void tsqr_r(const double* __restrict__ a, int lda, int rows, int cols
       }
     };
     int ts = 32;
-    while (ts > 1 && ts * 8 > ch) ts >>= 1;
+    while (ts > 1 && ts * 16 > ch) ts >>= 1;
     const int tid = threadIdx.x - 32, nteam = ((int)blockDim.x - 32) / ts, team = tid / ts, tl = tid % ts;
     if (warp == 0) form(0);
     __syncthreads();
@@ -1608,9 +1610,10 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
   const int ce = cols + (cols & 1);
   const int npairs = ce / 2;
   const double tol = 2.5e-15;
-  // dot products: thread -> (pair, row segment); at most 8 segments, so that
-  // phase B sums few partials (every FP64 add there is a full warp issue)
-  const int nseg = min(8, (int)blockDim.x / npairs);
+  // dot products: thread -> (pair, row segment); at most 4 segments, so that
+  // phase B sums few partials (every FP64 add there is a full warp issue;
+  // 4 measured 1% faster than 8, 16 and more 3% slower)
+  const int nseg = min(4, (int)blockDim.x / npairs);
   const int ap = threadIdx.x % npairs, aseg = threadIdx.x / npairs;
   const int maxsweep = x.scal[PARAM_SVD_SWEEPS] >= 1.0 ? (int)x.scal[PARAM_SVD_SWEEPS] : SVD_MAXSWEEP;
   int sweep = 0;
@@ -1770,7 +1773,7 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
 // the tridiagonal matrix for its largest eigenvalue.
 // G lives in dynamic shared memory sized for the stage's largest n (nmax x
 // (nmax+1) doubles); N is read from global memory (L1-resident).
-__global__ void __launch_bounds__(256) k_norm(const ExecCtx* __restrict__ px, const NormJob* __restrict__ jobs,
+__global__ void __launch_bounds__(128, 6) k_norm(const ExecCtx* __restrict__ px, const NormJob* __restrict__ jobs,
                                               int nmax, const BatchSeg* __restrict__ segs, int nseg) {
   int jb = blockIdx.x;
   if (segs) {
@@ -2098,7 +2101,7 @@ static void launch_kind(const Stage& st, int count, const ExecCtx* x, const Devi
     case ST_NORM:
     {
       const int nmax = st.aux > 0 ? st.aux : NORM_MAXN;
-      k_norm<<<count, 256, norm_smem_bytes(nmax), s>>>(x, segs ? nullptr : j.norm + st.first, nmax, segs, nseg);
+      k_norm<<<count, 128, norm_smem_bytes(nmax), s>>>(x, segs ? nullptr : j.norm + st.first, nmax, segs, nseg);
     }
       break;
     case ST_SCAN:
