@@ -15,7 +15,7 @@ structures and no blocking or reordering beyond what the paper states:
   from the identity theorem, Def. 3 / eq. (5), Def. 4);
 * basis products P_{XY,s} = W_{X,s}^* V_{Y,s} (Section 4.1);
 * basis trees with yield, mul, finish, add, split, uniform, nearfield
-  (Defs. 8-9, Section 4.2) and addproduct (Fig. 1);
+  (Defs. 8-9, Section 4.2) and the product added to a basis tree (Section 4.3);
 * accumulators with the four cases and splitting (Def. 5, Sections 3.2-3.3,
   basis-tree form of the split in Section 4.3);
 * coarsening by agglomeration with the row-then-column error control
@@ -859,31 +859,54 @@ class Side:
         return [(self.row(c), self.col(c), c) for c in b.children]
 
 
-def addproduct(side, b, S, a):
-    """Fig. 1: returns alpha' with yield(alpha') = yield(alpha) + Z|_{t x s} U_s S,
-    Z the side's matrix (X or Y^*), U its partner basis (V_Y or W_X)."""
-    t, s = side.row(b), side.col(b)
-    if b.is_leaf and b.adm:
-        beta = bt_uniform(t, mm(mm(side.coupling(b), side.Pmat(s)), S))
-        return bt_add(a, beta, side.basis)
-    if b.is_leaf:
-        Z = mm(side.near(b), mm(side.descend_basis.full(s), S))
-        beta = bt_nearfield(t, Z, a.C.shape[0])
-        return bt_add(a, beta, side.basis)
-    # subdivided block: make alpha split and finished, recurse into children (R7)
+def product_pieces(side, b, S):
+    """The basis trees whose yields sum to Z|_{t x s} U_s S (Section 4.3): the
+    block subtree of b walked level by level, the right factor carried down by
+    U_{s'} = U_s E_{s'} (eq. (5)), so a child block (t', s') gets E_{s'} S when
+    its column cluster is a child of s (S unchanged when s is a leaf).  Every
+    leaf block contributes at its row cluster t': an admissible leaf the basis
+    tree uniform(S_{t's'} P_{s'} S) of eq. (11), an inadmissible leaf
+    nearfield(N_{t's'} U_{s'} S) of eq. (10).  Returns [(t', beta)]."""
+    pieces = []
+    level = [(b, S)]
+    while level:
+        deeper = []
+        for blk, Sb in level:
+            t, s = side.row(blk), side.col(blk)
+            if blk.is_leaf:
+                if blk.adm:
+                    pieces.append((t, bt_uniform(t, mm(mm(side.coupling(blk), side.Pmat(s)), Sb))))
+                else:
+                    Z = mm(side.near(blk), mm(side.descend_basis.full(s), Sb))
+                    pieces.append((t, bt_nearfield(t, Z, side.basis.rank[t.id])))
+                continue
+            for _, sc, c in side.children(blk):
+                deeper.append((c, Sb if sc is s else mm(side.descend_basis.trans[sc.id], Sb)))
+        level = deeper
+    return pieces
+
+
+def deposit(a, tgt, beta, basis):
+    """yield(alpha) + yield(beta) restricted to the rows of tgt, tgt = alpha's
+    cluster or a descendant: add(alpha, beta) at tgt (Section 4.2), reached
+    through finish and split on the way down (both keep the yield)."""
+    if a.t is tgt:
+        return bt_add(a, beta, basis)
     a = bt_finish(a)
-    if not t.is_leaf and a.kids is None:
-        a = bt_split(a, side.basis)
-    kids = list(a.kids) if a.kids is not None else None
-    for tc, sc, c in side.children(b):
-        Sc = S if sc is s else mm(side.descend_basis.trans[sc.id], S)
-        if tc is t:
-            a = addproduct(side, c, Sc, a)
-            kids = list(a.kids) if a.kids is not None else None
-        else:
-            i = t.children.index(tc)
-            kids[i] = addproduct(side, c, Sc, kids[i])
-            a = BT(a.t, a.C, None, a.N, kids)
+    if a.kids is None:
+        a = bt_split(a, basis)
+    i = next(j for j, tc in enumerate(a.t.children) if tc.off <= tgt.off < tc.off + tc.size)
+    kids = list(a.kids)
+    kids[i] = deposit(kids[i], tgt, beta, basis)
+    return BT(a.t, a.C, None, None, kids)
+
+
+def addproduct(side, b, S, a):
+    """The basis tree alpha' with yield(alpha') = yield(alpha) + Z|_{t x s} U_s S,
+    Z the side's matrix (X or Y^*) and U its partner basis (V_Y or W_X)
+    (Section 4.3): the pieces of the product, each added at its row cluster."""
+    for tgt, beta in product_pieces(side, b, S):
+        a = deposit(a, tgt, beta, side.basis)
     return a
 
 
