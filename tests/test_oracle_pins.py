@@ -181,7 +181,7 @@ def test_basis_tree_operation_identities(small_h2):
 
 
 def test_addproduct_matches_dense(small_h2):
-    """Fig. 1: addproduct(X|_{t x s}, S, alpha) adds X|_{t x s} V_{Y,s} S."""
+    """Section 4.3: addproduct(X|_{t x s}, S, alpha) adds X|_{t x s} V_{Y,s} S."""
     X, Y = small_h2
     prod = O.Product(X, Y)
     rng = np.random.default_rng(5)
