@@ -106,12 +106,14 @@ constexpr int64_t WS_LOCAL_MASK = (int64_t(1) << WS_LOCAL_BITS) - 1;
 // Places the tagged workspace buffers of a finished product plan by lifetime
 // and rewrites every workspace pointer of its jobs; returns the workspace
 // length (doubles).  A buffer lives from the first to the last stage whose
-// jobs address it; buffers of the same lifetime are laid out as one group,
-// and the groups are placed first-fit in order of first use, a group's space
-// being free again from the stage after its last use.  Stages of one product
-// run in order (a chained GEMM stage waits for its product's previous one),
-// so two buffers share memory only when no stage can see both.  The
-// arithmetic of every job is unchanged: only addresses move.
+// jobs address it; buffers of the same lifetime are laid out as one group.
+// Groups are placed largest first, each at the lowest address that no
+// already placed group of overlapping lifetime occupies (offline placement
+// with known lifetimes; on the k = 64 sphere at n = 65536 it needs 1.04 times
+// the largest live total, against 1.36 for first-fit in order of first use).
+// Stages of one product run in order (a chained GEMM stage waits for its
+// product's previous one), so two buffers share memory only when no stage can
+// see both.  The arithmetic of every job is unchanged: only addresses move.
 static int64_t pack_workspace(Plan& P, const std::vector<int64_t>& bufs) {
   const size_t nb = bufs.size();
   std::vector<int> first(nb, INT_MAX), last(nb, -1);
@@ -151,64 +153,37 @@ static int64_t pack_workspace(Plan& P, const std::vector<int64_t>& bufs) {
     }
   };
   each_ptr([&](Ptr& p, int s) { touch(p, s); });
-  // groups of equal lifetime, in order of first use
+  // groups of equal lifetime
   std::map<std::pair<int, int>, int64_t> gsize;
   for (size_t i = 0; i < nb; ++i)
     if (last[i] >= 0) gsize[{first[i], last[i]}] += bufs[i];
-  std::map<std::pair<int, int>, int64_t> gbase;
-  std::map<int64_t, int64_t> freel;  // free extents below `top`: start -> length
-  std::vector<std::pair<int, std::pair<int, int>>> frees;  // (stage at which free, group)
-  int64_t top = 0;
-  auto release = [&](int64_t st, int64_t len) {
-    int64_t en = st + len;
-    auto it = freel.lower_bound(st);
-    if (it != freel.end() && it->first == en) {
-      en += it->second;
-      it = freel.erase(it);
-    }
-    if (it != freel.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == st) {
-        st = pv->first;
-        freel.erase(pv);
-      }
-    }
-    if (en == top) top = st;
-    else freel[st] = en - st;
-    // a free extent that now ends at top shrinks top
-    while (!freel.empty()) {
-      auto lastf = std::prev(freel.end());
-      if (lastf->first + lastf->second != top) break;
-      top = lastf->first;
-      freel.erase(lastf);
-    }
+  struct Grp {
+    int first, last;
+    int64_t len, base;
   };
-  std::multimap<int, std::pair<int, int>> ends;  // last stage -> group
+  std::vector<Grp> gs;
+  gs.reserve(gsize.size());
+  for (const auto& [g, len] : gsize) gs.push_back(Grp{g.first, g.second, len, 0});
+  std::stable_sort(gs.begin(), gs.end(), [](const Grp& a, const Grp& b) { return a.len > b.len; });
+  std::map<std::pair<int, int>, int64_t> gbase;
   int64_t peak = 0;
-  for (const auto& [g, len] : gsize) {
-    const int s = g.first;
-    // free every group whose last use lies before stage s
-    while (!ends.empty() && ends.begin()->first < s) {
-      const auto gg = ends.begin()->second;
-      release(gbase[gg], gsize[gg]);
-      ends.erase(ends.begin());
+  std::vector<std::pair<int64_t, int64_t>> busy;  // address ranges of overlapping placed groups
+  for (size_t gi = 0; gi < gs.size(); ++gi) {
+    Grp& g = gs[gi];
+    busy.clear();
+    for (size_t pj = 0; pj < gi; ++pj) {
+      const Grp& o = gs[pj];
+      if (o.last >= g.first && o.first <= g.last) busy.push_back({o.base, o.base + o.len});
     }
-    int64_t got = -1;
-    for (auto it = freel.begin(); it != freel.end(); ++it)
-      if (it->second >= len) {
-        got = it->first;
-        const int64_t rem = it->second - len;
-        freel.erase(it);
-        if (rem) freel[got + len] = rem;
-        break;
-      }
-    if (got < 0) {
-      got = top;
-      top += len;
+    std::sort(busy.begin(), busy.end());
+    int64_t at = 0;
+    for (const auto& [b0, b1] : busy) {
+      if (b0 - at >= g.len) break;
+      at = std::max(at, b1);
     }
-    peak = std::max(peak, top);
-    gbase[g] = got;
-    ends.insert({g.second, g});
+    g.base = at;
+    gbase[{g.first, g.last}] = at;
+    peak = std::max(peak, at + g.len);
   }
   // buffer bases: consecutive inside their group
   std::vector<int64_t> base(nb, 0);
