@@ -41,6 +41,9 @@ UNIT = "products/s"
 GRID = 128
 EPS = 1e-6
 KIND_NAMES = ["k_gemm", "k_copy", "k_qr", "k_qapply", "k_svd", "k_scan", "k_finalize", "k_norm"]
+# profile kind 8: the tensor-core GEMM stages again (a subset of k_gemm), with
+# the multiply-adds issued to the tensor cores as their flops
+TC_KIND = "k_gemm_tc"
 
 
 def workload_config(grid=GRID):
@@ -63,13 +66,23 @@ def load_json(*parts):
 ORACLE_KIND = {"k_gemm": ("gemm",), "k_qr": ("qr",), "k_qapply": (), "k_svd": ("svd",), "k_norm": ("norm",)}
 
 
-def kernel_table(kinds, mw, peak, hbm_peak):
+def kernel_table(kinds, mw, peak, hbm_peak, tc=None, bf16_peak=None):
     """Per kernel of the profiled product: launches, time, executed and
     oracle-counted work, and the fraction of its roofline (FP64 ALU peak for
     the arithmetic kernels, HBM copy bandwidth for k_copy).  k_gemm mixes
     tensor-core and compensated-FP32 stages; its fraction is against the FP64
-    peak the plain form would be bound by."""
+    peak the plain form would be bound by.  tc: the tensor-core stages of
+    k_gemm, their multiply-adds on the tensor cores against the BF16 peak."""
     out = {}
+    if tc is not None and tc.launches:
+        s = tc.ms / 1e3
+        out[TC_KIND + " (tensor-core stages of k_gemm)"] = {
+            "launches": tc.launches, "jobs": tc.jobs, "ms": round(tc.ms, 4),
+            "tensor_tflops": round(tc.flops / s / 1e12, 3) if s > 0 else None,
+            "bf16_peak_tflops": bf16_peak,
+            "frac_tensor": round(tc.flops / s / 1e12 / bf16_peak, 4) if (s > 0 and bf16_peak) else None,
+            "what": "BF16 slice products issued (mma.sync m16n8k16, padding included) per second, against the "
+                    "measured BF16 burst peak"}
     for nm, p_ in kinds:
         if p_.launches == 0:
             continue
@@ -452,7 +465,7 @@ def main():
 
     # roofline of the dominant kernel of the chosen form: one profiled product
     # (stages one by one, CUDA events around each)
-    prof = (h2.KernelProf * len(KIND_NAMES))()
+    prof = (h2.KernelProf * h2.PROFILE_KINDS)()
     Cp = h2.mul_profile(A, B, EPS, prof, stream=sptr, precision=4)
     Cp.free()
     kinds = [(KIND_NAMES[i], prof[i]) for i in range(len(KIND_NAMES))]
@@ -531,7 +544,8 @@ def main():
                                       "peak_gbs": hbm_peak,
                                       "frac": (kc.bytes / (kc.ms / 1e3) / 1e9) / hbm_peak
                                       if (kc.ms > 0 and hbm_peak) else None} if kc else None},
-            "kernels": kernel_table(kinds, mw, peak, hbm_peak),
+            "kernels": kernel_table(kinds, mw, peak, hbm_peak, tc=prof[len(KIND_NAMES)],
+                                    bf16_peak=(load_json("MEASURED_PEAKS.json") or {}).get("bf16_tflops")),
             "product": {"nadm": st0.nadm, "ninadm": st0.ninadm, "agglomerated": st0.nagglomerated,
                         "rank_max": max(st0.row_rank_max, st0.col_rank_max), "workspace_gb": st0.workspace_bytes / 1e9,
                         "rank_max_chosen": max(st_c.row_rank_max, st_c.col_rank_max)},

@@ -143,14 +143,18 @@ int h2_mul(const h2_matrix* A, const h2_matrix* B, double eps, const h2_mul_opts
 /* Measurement helper (not part of the method): per kernel kind, the launches,
  * summed device time (CUDA events around every stage on the product's stream)
  * and the algorithmic work of one product computed like h2_mul.  Kinds:
- * 0 batched GEMM, 1 copy, 2 Householder QR, 3 Q application, 4 Jacobi SVD,
- * 5 rank prefix sums, 6 finalize, 7 block norms.  flops count the FP64 operations of the
- * algorithm with the ranks the device decided (Householder QR 2mn^2 - 2n^3/3;
- * one-sided Jacobi m n (n-1) + 2mn per executed sweep plus 6m per applied
- * rotation); bytes are the algorithmic
- * reads and writes of each job.  The stages run one by one (no graph).
- * `out` must hold H2_PROFILE_KINDS entries.  The product is returned in *C. */
-#define H2_PROFILE_KINDS 8
+ * 0 batched GEMM (every arithmetic mode), 1 copy, 2 Householder QR, 3 Q
+ * application, 4 Jacobi SVD, 5 rank prefix sums, 6 finalize, 7 block norms,
+ * 8 the tensor-core GEMM stages again (a subset of kind 0).  flops count the
+ * FP64 operations of the algorithm with the ranks the device decided
+ * (Householder QR 2mn^2 - 2n^3/3; one-sided Jacobi m n (n-1) + 2mn per
+ * executed sweep plus 6m per applied rotation); for kind 8 they count the
+ * multiply-adds issued to the tensor cores instead (2 x 16 x 8 x 16 per BF16
+ * slice product of mma.sync m16n8k16, S(S+1)/2 of them per tile and k step,
+ * padding included).  bytes are the algorithmic reads and writes of each job.
+ * The stages run one by one (no graph).  `out` must hold H2_PROFILE_KINDS
+ * entries.  The product is returned in *C. */
+#define H2_PROFILE_KINDS 9
 typedef struct {
   int launches;
   int jobs;

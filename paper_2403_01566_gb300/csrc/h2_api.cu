@@ -298,7 +298,17 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
     if (i == ns) continue;
     const Stage& st = P.stages[i];
     pr.jobs += st.count;
-    double st_fl = 0.0;
+    double st_fl = 0.0, st_tfl = 0.0, st_by = 0.0;
+    // tensor-core GEMM stages: multiply-adds issued to the tensor cores, as
+    // mma.sync m16n8k16 slice products (S(S+1)/2 per 16 x 8 tile and k step of
+    // 16; k chunks of 32, the last one rounded up to 16)
+    const int tc_slices = st.kind == ST_GEMM ? gemm_shape(st.aux).slices : 0;
+    auto tc_flops = [&](double mm, double nn, double kk) {
+      if (mm <= 0 || nn <= 0 || kk <= 0) return 0.0;
+      const double full = std::floor(kk / 32.0), rem = kk - 32.0 * full;
+      const double ksteps = 2.0 * full + std::ceil(rem / 16.0);
+      return std::ceil(mm / 16.0) * std::ceil(nn / 8.0) * ksteps * (tc_slices * (tc_slices + 1) / 2) * 4096.0;
+    };
     double sw_sum = 0.0, sw_max = 0.0, rows_sum = 0.0, cols_sum = 0.0, rows_max = 0.0, cols_max = 0.0;
     double glob_jobs = 0.0, glob_fl = 0.0;  // SVD jobs whose matrix stays in global memory
     for (int j = 0; j < st.count; ++j) {
@@ -319,10 +329,12 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
               const double k1 = dv(T.k1);
               fl += 2 * m * n * k1;
               by += 8 * (m * k1 + k1 * n);
+              if (tc_slices) st_tfl += tc_flops(m, n, k1);
             } else {
               const double k1 = dv(T.k1), k2 = dv(T.k2);
               fl += 2 * m * k1 * k2 + 2 * m * k2 * n;
               by += 8 * (m * k1 + k1 * k2 + k2 * n);
+              if (tc_slices) st_tfl += tc_flops(m, k2, k1) + tc_flops(m, n, k2);
             }
           }
           break;
@@ -385,6 +397,15 @@ static int run_plan_profiled(PlanRT& rt, double* bx, double* by, double* bc, int
       pr.flops += fl;
       pr.bytes += by;
       st_fl += fl;
+      st_by += by;
+    }
+    if (tc_slices) {
+      h2_kernel_prof& tc = prof[8];
+      tc.launches += stage_launches(st);
+      tc.jobs += st.count;
+      tc.ms += ms;
+      tc.flops += st_tfl;
+      tc.bytes += st_by;
     }
     if (verbose) {
       std::fprintf(stderr, "stage %4zu kind %d tag %2d jobs %7d smem %6d ms %9.4f gflop %9.4f tflops %6.3f", i,

@@ -313,10 +313,16 @@ class Server:
             pass
 
 
+PROFILE_KINDS = 9  # H2_PROFILE_KINDS
+
+
 def mul_profile(A: H2Matrix, B: H2Matrix, eps: float, prof, max_rank: int = 0, stream=None,
                 precision: int = 0) -> H2Matrix:
     """h2_mul_profile: the product with per-kernel-kind device times and work in `prof`
-    (an array of 8 KernelProf)."""
+    (an array of PROFILE_KINDS KernelProf; kind 8 repeats the tensor-core GEMM
+    stages with their tensor-core multiply-add work)."""
+    if len(prof) < PROFILE_KINDS:
+        raise ValueError(f"prof needs {PROFILE_KINDS} entries")
     o = MulOpts()
     o.theta, o.max_rank, o.precision, o.sync = 0.0, int(max_rank), int(precision), 1
     o.stream = stream
