@@ -185,6 +185,13 @@ static int64_t pack_workspace(Plan& P, const std::vector<int64_t>& bufs) {
     gbase[{g.first, g.last}] = at;
     peak = std::max(peak, at + g.len);
   }
+  // invariant: groups whose lifetimes overlap occupy disjoint addresses
+  for (size_t a = 0; a < gs.size(); ++a)
+    for (size_t b = a + 1; b < gs.size(); ++b) {
+      const Grp &x = gs[a], &y = gs[b];
+      if (x.last >= y.first && y.last >= x.first && x.base < y.base + y.len && y.base < x.base + x.len)
+        throw std::runtime_error("workspace placement overlaps two live buffers");
+    }
   // buffer bases: consecutive inside their group
   std::vector<int64_t> base(nb, 0);
   std::map<std::pair<int, int>, int64_t> gnext = gbase;
