@@ -592,51 +592,67 @@ constexpr int TC_NE = (64 * TK) / 256;  // elements of an operand chunk per thre
 // Slices go to dst[p][r][k] (row length TKP), the exponents to rexp[r].
 // along: a warp holds one row (lane = k), its maximum is a warp reduction;
 // otherwise the maxima meet in shared memory (zeroed by the caller) and a
-// second pass slices.
+// second pass slices.  Each thread issues all of its loads before it slices
+// (8 in flight instead of one; the GEMM stages of a product 21.8 -> 19.5 ms).
 template <int S, bool PAIR>
 __device__ __forceinline__ void tc_stage(uint16_t* dst, int R16, int* rexp, const TcSrc& X, bool along, int rows,
                                          int k0, int kc) {
   const int total = R16 * TK;
   const int pstride = R16 * TKP;
   if (along) {
-#pragma unroll 1
+    // all of this thread's loads first (independent, in flight together)
+    TcRaw v[TC_NE];
+#pragma unroll
+    for (int it = 0; it < TC_NE; ++it) {
+      const int e = threadIdx.x + 256 * it;
+      const int r = e / TK, k = e % TK;
+      v[it] = TcRaw{0ull};
+      if (e < total && r < rows && k < kc) {
+        if (PAIR) v[it] = raw_of_pair(X.s[r * X.ld + k0 + k]);
+        else v[it] = raw_of_double(X.g[(int64_t)r * X.ld + k0 + k]);
+      }
+    }
+#pragma unroll
     for (int it = 0; it < TC_NE; ++it) {
       const int e = threadIdx.x + 256 * it;
       if (e >= total) break;
       const int r = e / TK, k = e % TK;
-      TcRaw v{0ull};
-      if (r < rows && k < kc) {
-        if (PAIR) v = raw_of_pair(X.s[r * X.ld + k0 + k]);
-        else v = raw_of_double(X.g[(int64_t)r * X.ld + k0 + k]);
-      }
-      const int Emax = __reduce_max_sync(0xffffffffu, raw_exp<PAIR>(v));
+      const TcRaw vi = v[it];
+      const int Emax = __reduce_max_sync(0xffffffffu, raw_exp<PAIR>(vi));
       if ((threadIdx.x & 31) == 0) rexp[r] = Emax;
-      put_raw_slices<S, PAIR>(dst + r * TKP + k, pstride, v, Emax);
+      put_raw_slices<S, PAIR>(dst + r * TKP + k, pstride, vi, Emax);
     }
     return;
   }
-  // two passes over the elements (the second read hits L1).  A warp takes
-  // a block of 8 rows x 4 k: 64-byte runs of consecutive r in memory, and
-  // slice stores into 16 distinct banks (row length TKP = 20 words).
+  // two passes over the elements held in registers.  A warp takes a block of
+  // 8 rows x 4 k: 64-byte runs of consecutive r in memory, and slice stores
+  // into 16 distinct banks (row length TKP = 20 words).
   const int nrb = R16 >> 3;
-#pragma unroll 1
+  TcRaw v[TC_NE];
+#pragma unroll
+  for (int it = 0; it < TC_NE; ++it) {
+    const int e = threadIdx.x + 256 * it;
+    const int b = e >> 5, ln = e & 31;
+    const int r = (b % nrb) * 8 + (ln & 7), k = (b / nrb) * 4 + (ln >> 3);
+    v[it] = (e < total && r < rows && k < kc) ? raw_of_double(X.g[(int64_t)(k0 + k) * X.ld + r]) : TcRaw{0ull};
+  }
+#pragma unroll
   for (int it = 0; it < TC_NE; ++it) {
     const int e = threadIdx.x + 256 * it;
     if (e >= total) break;
     const int b = e >> 5, ln = e & 31;
-    const int r = (b % nrb) * 8 + (ln & 7), k = (b / nrb) * 4 + (ln >> 3);
-    const int E = (r < rows && k < kc) ? raw_exp<false>(raw_of_double(X.g[(int64_t)(k0 + k) * X.ld + r])) : 0;
+    const int r = (b % nrb) * 8 + (ln & 7);
+    const int E = raw_exp<false>(v[it]);
     if (E) atomicMax(&rexp[r], E);
   }
   __syncthreads();
-#pragma unroll 1
+#pragma unroll
   for (int it = 0; it < TC_NE; ++it) {
     const int e = threadIdx.x + 256 * it;
     if (e >= total) break;
     const int b = e >> 5, ln = e & 31;
     const int r = (b % nrb) * 8 + (ln & 7), k = (b / nrb) * 4 + (ln >> 3);
-    const TcRaw v = (r < rows && k < kc) ? raw_of_double(X.g[(int64_t)(k0 + k) * X.ld + r]) : TcRaw{0ull};
-    put_raw_slices<S, false>(dst + r * TKP + k, pstride, v, rexp[r]);
+    put_raw_slices<S, false>(dst + r * TKP + k, pstride, v[it], rexp[r]);
   }
 }
 
