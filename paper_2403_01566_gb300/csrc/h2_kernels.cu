@@ -1197,9 +1197,18 @@ __device__ void tsqr_r(const double* __restrict__ a, int lda, int rows, int cols
   for (int e = threadIdx.x; e < cols * cols; e += blockDim.x) W[(e / cols) * ld + e % cols] = 0.0;
   for (int r0 = 0; r0 < rows; r0 += ch_max) {
     const int ch = min(ch_max, rows - r0);
-    for (int e = threadIdx.x; e < ch * cols; e += blockDim.x) {
-      const int c = e / ch, i = e % ch;
-      C[c * ld + i] = a[(int64_t)c * lda + r0 + i];
+    for (int e0 = threadIdx.x; e0 < ch * cols; e0 += 8 * blockDim.x) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = e < ch * cols ? a[(int64_t)(e / ch) * lda + r0 + e % ch] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < ch * cols) C[(e / ch) * ld + e % ch] = v[u];
+      }
     }
     __syncthreads();
     // one step of look-ahead, as in householder_cols_la: while warps 1..
@@ -1316,9 +1325,21 @@ __global__ void __launch_bounds__(256) k_qr(const ExecCtx* __restrict__ px, cons
   }
   if ((int64_t)rows * cols <= smem_doubles) {
     // whole matrix in shared memory
-    for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
-      const int c = (int)(e / rows), i = (int)(e % rows);
-      sm[e] = a[(int64_t)c * lda + i];
+    {
+      const int64_t tot = (int64_t)rows * cols;
+      for (int64_t e0 = threadIdx.x; e0 < tot; e0 += 8 * (int64_t)blockDim.x) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t e = e0 + (int64_t)u * blockDim.x;
+          v[u] = e < tot ? a[(int64_t)(e / rows) * lda + e % rows] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t e = e0 + (int64_t)u * blockDim.x;
+          if (e < tot) sm[e] = v[u];
+        }
+      }
     }
     __syncthreads();
     const int rk = householder_cols(sm, rows, rows, cols, tau, sh, piv, cn, cn0, floor2);
