@@ -1058,17 +1058,23 @@ __device__ int householder_cols(double* a, int lda, int rows, int cols, double* 
     if (warp == 0) {
       bool stop = false;
       if (piv) {
-        double bv = -1.0, rs = 0.0;
+        // largest trailing norm: the norms are never negative, so their
+        // FP64 bit patterns order like the values and compare as integers
+        // (no FP64 instruction on this serial step)
+        long long bv = -1;
+        double rs = 0.0;
         int bi = j;
         for (int c = j + lane; c < cols; c += 32) {
-          rs += cn[c];
-          if (cn[c] > bv) {
-            bv = cn[c];
+          const double v = cn[c];
+          if (thr >= 0.0) rs += v;
+          const long long vb = __double_as_longlong(v);
+          if (vb > bv) {
+            bv = vb;
             bi = c;
           }
         }
         for (int o = 16; o > 0; o >>= 1) {
-          const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ov > bv || (ov == bv && oi < bi)) {
             bv = ov;
@@ -1685,8 +1691,12 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
           for (int sg = 1; sg < nseg; ++sg) gt += part[sg * npairs + p];
           const double di = dsc[i], dj = dsc[j];
           const double ga = gt * di * dj, al = nrm2[i], be = nrm2[j];
-          // |ga| > tol * sqrt(al * be), in squared form
-          if (ga != 0.0 && al > tiny2 && be > tiny2 && ga * ga > (tol * tol) * al * be) {
+          // |ga| > tol * sqrt(al * be), in squared form; the squared norms and
+          // the floor are never negative, so those tests compare FP64 bit
+          // patterns as integers (no FP64 instruction)
+          const long long tb = __double_as_longlong(tiny2);
+          if ((__double_as_longlong(ga) << 1) != 0 && __double_as_longlong(al) > tb &&
+              __double_as_longlong(be) > tb && ga * ga > (tol * tol) * al * be) {
             // t = tan(theta), the smaller root of f(t) = g2 t^2 + 2 d t - g2
             // (d = be - al, g2 = 2 ga): first in FP32 as
             // t = sign(d) g2 / (|d| + sqrt(d^2 + g2^2)) from d and g2 scaled by
