@@ -1857,45 +1857,57 @@ __global__ void __launch_bounds__(128, 6) k_norm(const ExecCtx* __restrict__ px,
     G[j * ld + i] = a;
   }
   __syncthreads();
-  // tridiagonalisation: for column k, reflect rows/cols k+1..n-1
+  // tridiagonalisation: for column k, reflect rows/cols k+1..n-1.  Four
+  // barriers a step: warp 0 forms the reflector (its norm a warp sum) and v;
+  // p = tau A v with two threads per row (halves of the row, one shuffle);
+  // every warp forms p.v itself (the same value in all) and w; the rank-2
+  // update.
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = 0; k + 2 < n; ++k) {
-    double s2 = 0.0;
-    for (int i = k + 2 + threadIdx.x; i < n; i += blockDim.x) s2 = fma(G[i * ld + k], G[i * ld + k], s2);
-    s2 = block_sum(s2, red);
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+      double s2 = 0.0;
+      for (int i = k + 2 + lane; i < n; i += 32) s2 = fma(G[i * ld + k], G[i * ld + k], s2);
+      s2 = warp_sum(s2);
       const double alpha = G[(k + 1) * ld + k];
       double tau = 0.0, sc = 0.0, beta = alpha;
       if (s2 > 0.0) householder_scalars(alpha, s2, beta, tau, sc);
-      sh[0] = tau;
-      sh[1] = sc;
-      e[k] = beta;
-      d[k] = G[k * ld + k];
+      if (lane == 0) {
+        sh[k & 1] = tau;  // two slots: a step without reflection has one barrier
+        e[k] = beta;
+        d[k] = G[k * ld + k];
+      }
+      if (tau != 0.0)
+        for (int i = k + 1 + lane; i < n; i += 32) v[i] = (i == k + 1) ? 1.0 : G[i * ld + k] * sc;
     }
     __syncthreads();
-    const double tau = sh[0], sc = sh[1];
+    const double tau = sh[k & 1];
     if (tau == 0.0) continue;
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) v[i] = (i == k + 1) ? 1.0 : G[i * ld + k] * sc;
-    __syncthreads();
-    // p = tau * A v on the trailing block A = G[k+1.., k+1..]
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+    const int m = n - k - 1, half = (m + 1) >> 1;
+    for (int base = 0; base < 2 * m; base += blockDim.x) {
+      const int r2 = base + threadIdx.x;
+      const int i = k + 1 + (r2 >> 1), h = r2 & 1;
       double a = 0.0;
-      for (int j = k + 1; j < n; ++j) a = fma(G[i * ld + j], v[j], a);
-      p[i] = tau * a;
+      if (r2 < 2 * m) {
+        const int j0 = k + 1 + h * half, j1 = h ? n : k + 1 + half;
+        for (int j = j0; j < j1; ++j) a = fma(G[i * ld + j], v[j], a);
+      }
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      if (r2 < 2 * m && h == 0) p[i] = tau * a;
     }
     __syncthreads();
     double pv = 0.0;
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) pv = fma(p[i], v[i], pv);
-    pv = block_sum(pv, red);
+    for (int i = k + 1 + lane; i < n; i += 32) pv = fma(p[i], v[i], pv);
+    pv = warp_sum(pv);
     const double K = 0.5 * tau * pv;
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) w[i] = p[i] - K * v[i];
     __syncthreads();
-    const int m = n - k - 1;
     for (int e2 = threadIdx.x; e2 < m * m; e2 += blockDim.x) {
       const int i = k + 1 + e2 / m, j = k + 1 + e2 % m;
       G[i * ld + j] -= v[i] * w[j] + w[i] * v[j];
     }
     __syncthreads();
   }
+  __syncthreads();  // every warp has read the last step's tau
   if (threadIdx.x == 0) {
     if (n >= 2) {
       d[n - 2] = G[(n - 2) * ld + (n - 2)];
