@@ -96,7 +96,9 @@ struct GemmPol<GM_F64> {
   __device__ static A zero() { return 0.0; }
   __device__ static O ozero() { return 0.0; }
   __device__ static void fma_acc(A& a, S x, S y) { a = fma(x, y, a); }
-  __device__ static void oadd(O& o, double alpha, const A& a) { o = fma(alpha, a, o); }
+  using Alpha = double;
+  __device__ static Alpha alpha_of(double alpha) { return alpha; }
+  __device__ static void oadd(O& o, Alpha alpha, const A& a) { o = fma(alpha, a, o); }
   __device__ static void oadd_plain(O& o, double alpha, double v) { o = fma(alpha, v, o); }
   __device__ static double result(const O& o) { return o; }
 };
@@ -111,18 +113,43 @@ struct GemmPol<GM_F32> {
   __device__ static A zero() { return 0.0f; }
   __device__ static O ozero() { return 0.0; }
   __device__ static void fma_acc(A& a, S x, S y) { a = fmaf(x, y, a); }
-  __device__ static void oadd(O& o, double alpha, const A& a) { o = fma(alpha, (double)a, o); }
+  using Alpha = double;
+  __device__ static Alpha alpha_of(double alpha) { return alpha; }
+  __device__ static void oadd(O& o, Alpha alpha, const A& a) { o = fma(alpha, (double)a, o); }
   __device__ static void oadd_plain(O& o, double alpha, double v) { o = fma(alpha, v, o); }
   __device__ static double result(const O& o) { return o; }
 };
 
-// Split of an FP64 value into FP32 hi + lo without FP64 instructions (on this
-// GPU every FP64 instruction, conversions included, issues at 1/64 of the
-// FP32 rate).  hi = the value truncated to 24 significant bits (bit copy of
-// sign, re-biased exponent and the top 23 fraction bits); lo = the remaining
-// 29 fraction bits rounded to FP32 and scaled: |v - hi - lo| <= 2^-47 |v|.
-// Zero and values below FP32's normal range (|v| < 2^-126) give (0, 0);
-// |v| >= 2^128, inf and NaN take the plain conversion.
+// FP32 value of an integer 0 <= m < 2^29 rounded to nearest even, by integer
+// operations only (on this GPU int-to-float conversions issue on the FP64
+// pipe, 16 cycles a warp instruction; the same bits as __uint2float_rn).
+__device__ __forceinline__ float f32_of_u29_rn(uint32_t m) {
+  if (m == 0u) return 0.0f;
+  const int p = 31 - __clz(m);  // leading bit
+  uint32_t mant;
+  int e = p;
+  if (p <= 23) {
+    mant = m << (23 - p);
+  } else {
+    const int sh = p - 23;  // 1..5
+    mant = m >> sh;
+    const uint32_t rem = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1u))) ++mant;
+    if (mant == (1u << 24)) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  return __uint_as_float(((uint32_t)(e + 127) << 23) | (mant & 0x7fffffu));
+}
+
+// Split of an FP64 value into FP32 hi + lo without FP64-pipe instructions
+// (on this GPU every FP64 instruction, conversions included, issues at 1/64
+// of the FP32 rate).  hi = the value truncated to 24 significant bits (bit
+// copy of sign, re-biased exponent and the top 23 fraction bits); lo = the
+// remaining 29 fraction bits rounded to FP32 and scaled: |v - hi - lo| <=
+// 2^-47 |v|.  Zero and values below FP32's normal range (|v| < 2^-126) give
+// (0, 0); |v| >= 2^128, inf and NaN take the plain conversion.
 __device__ __forceinline__ float2 split_df(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
@@ -135,9 +162,20 @@ __device__ __forceinline__ float2 split_df(double v) {
   const unsigned sign = hw & 0x80000000u;
   const unsigned ebits = (unsigned)(e + 127) << 23;
   const float hi = __uint_as_float(sign | ebits | ((hw & 0xfffffu) << 3) | (lw >> 29));
-  const float rem = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), 0x1p-52f);  // < 2^-23
-  const float lo = __fmul_rn(rem, __uint_as_float(ebits));                    // rem * 2^e
+  const float rem = __fmul_rn(f32_of_u29_rn(lw & 0x1fffffffu), 0x1p-52f);  // < 2^-23
+  const float lo = __fmul_rn(rem, __uint_as_float(ebits));                  // rem * 2^e
   return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
+
+// Exact FP64 value of an FP32 value, by bit operations for normal values and
+// zero (float-to-double conversions also issue on the FP64 pipe).
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t ef = (b >> 23) & 0xffu;
+  if (ef == 0u && (b & 0x7fffffu) != 0u) return (double)f;  // subnormal
+  if (ef == 0xffu) return (double)f;                        // inf, NaN
+  const uint32_t hw = (b & 0x80000000u) | (ef ? ((ef - 127u + 1023u) << 20) : 0u) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hw, (int)((b & 0x7u) << 29));
 }
 
 template <>
@@ -154,9 +192,10 @@ struct GemmPol<GM_DF> {
   __device__ static A zero() { return DF{0.0f, 0.0f}; }
   __device__ static O ozero() { return DF{0.0f, 0.0f}; }
   // o += (ph + pl) with ph = alpha_hi * a.s exact through an FMA: TwoSum on
-  // the leading parts, every error term into o.c
-  __device__ static void oadd(O& o, double alpha, const A& a) {
-    const float2 al = split_df(alpha);
+  // the leading parts, every error term into o.c (alpha split once per term)
+  using Alpha = float2;
+  __device__ static Alpha alpha_of(double alpha) { return split_df(alpha); }
+  __device__ static void oadd(O& o, Alpha al, const A& a) {
     const float ph = __fmul_rn(al.x, a.s);
     float pl = fmaf(al.x, a.s, -ph);
     pl = fmaf(al.x, a.c, pl);
@@ -174,7 +213,7 @@ struct GemmPol<GM_DF> {
     o.s = t;
     o.c = __fadd_rn(__fadd_rn(o.c, err), l);
   }
-  __device__ static double result(const O& o) { return (double)o.s + (double)o.c; }
+  __device__ static double result(const O& o) { return f64_of_f32(o.s) + f64_of_f32(o.c); }
   // The error terms of one step are summed first, so that each of a.s and
   // a.c carries a single dependent add from one k step to the next.
   __device__ static void fma_acc(A& a, S x, S y) {
@@ -321,9 +360,10 @@ __device__ __forceinline__ void gemm_job(const ExecCtx& x, const GemmOut& O, con
     for (int q = 0; q < Q; ++q) tacc[q] = P::zero();
     if (C == nullptr) {
       gemm_accumulate<Q, MODE>(tacc, om, m, n, k1, A, Tm.lda, Tm.ta, B, Tm.ldb, Tm.tb, As, Bs, ldbs);
+      const typename P::Alpha al = P::alpha_of(alpha);
 #pragma unroll
       for (int q = 0; q < Q; ++q)
-        if (q < om.nv) P::oadd(acc[q], alpha, tacc[q]);
+        if (q < om.nv) P::oadd(acc[q], al, tacc[q]);
       continue;
     }
     // three-factor term: Ts = op(A)op(B) (m x nn), then acc += alpha * Ts op(C)
@@ -351,9 +391,10 @@ __device__ __forceinline__ void gemm_job(const ExecCtx& x, const GemmOut& O, con
       mac_rows<Q, MODE>(tacc, om.nv, tr + kk, tstep, Bs + om.c, ldbs, kc);
       __syncthreads();
     }
+    const typename P::Alpha al = P::alpha_of(alpha);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
-      if (q < om.nv) P::oadd(acc[q], alpha, tacc[q]);
+      if (q < om.nv) P::oadd(acc[q], al, tacc[q]);
   }
   double* out = ptrv(O.o, x);
 #pragma unroll
