@@ -167,3 +167,33 @@ def test_precision_values():
     C1 = h2.mul(A, A, 1e-6, precision=1)
     C0 = h2.mul(A, A, 1e-6, precision=0)
     assert np.isfinite(C1.to_dense()).all() and np.isfinite(C0.to_dense()).all()
+
+
+def test_profile_kinds_and_tensor_core_subset():
+    """h2_mul_profile: the product it returns equals h2_mul's; kind 8 repeats
+    the tensor-core GEMM stages (a subset of kind 0 in launches, jobs and
+    time) with the slice products they issue (S(S+1)/2 = 28 mma.sync
+    m16n8k16 per 16 x 8 tile and k step), at a rate below the tensor cores'
+    peak; the FP64 form issues none."""
+    w = I.grid_2d(64)
+    A = h2.build(w.points, w.kernel_a, w.eta, w.leaf_size, w.order)
+    B = h2.build(w.points, w.kernel_b, w.eta, w.leaf_size, w.order)
+    with pytest.raises(ValueError):
+        h2.mul_profile(A, B, 1e-6, (h2.KernelProf * 8)(), precision=4)
+    for prec in (0, 4):
+        prof = (h2.KernelProf * h2.PROFILE_KINDS)()
+        Cp = h2.mul_profile(A, B, 1e-6, prof, precision=prec)
+        C = h2.mul(A, B, 1e-6, precision=prec)
+        assert np.array_equal(Cp.to_dense(), C.to_dense())
+        tc, gemm = prof[8], prof[0]
+        if prec == 0:
+            assert tc.launches == 0 and tc.flops == 0.0
+            continue
+        assert 0 < tc.launches <= gemm.launches and 0 < tc.jobs <= gemm.jobs
+        assert 0.0 < tc.ms <= gemm.ms
+        rate = tc.flops / (tc.ms / 1e3)  # slice products issued per second
+        assert 1e12 < rate < 2.5e15, rate  # below the tensor cores' dense BF16 peak
+        # every profiled kind's time is positive where it launched
+        for k in range(h2.PROFILE_KINDS):
+            if prof[k].launches:
+                assert prof[k].ms > 0.0
