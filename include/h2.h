@@ -314,10 +314,10 @@ int h2_permutation(const h2_matrix* A, int64_t* perm);
  * on every GPU that loads the library, held until exit.  A call needs
  * 2 * nclusters * kpad doubles of it and returns H2_ENOMEM beyond that.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array, which keeps the last call's contents (each call
- * clears what must start at zero): calls that overlap on the GPU race, so
- * serialise them (host threads are serialised by the call itself). */
+ * (cudaGetSymbolAddress).  All calls share the array, which keeps the last
+ * call's contents (each call clears what must start at zero): calls that
+ * overlap on the GPU race, so serialise them (host threads are serialised by
+ * the call itself). */
 int h2_matvec_noalloc(const h2_matrix* A, const double* x, double* y, void* stream);
 
 void h2_free(h2_matrix* A);
