@@ -1617,7 +1617,7 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
   if (rows <= 0 || cols <= 0) {
     if (threadIdx.x == 0) {
       if (rank_out) *rank_out = 0;
-      if (J.mode == 4) {
+      if (J.norm_idx >= 0) {
         x.nrm[J.norm_idx] = 0.0;
         x.scal[J.norm_idx] = 0.0;
       }
@@ -1841,7 +1841,8 @@ __global__ void __launch_bounds__(256, 3) k_svd(const ExecCtx* __restrict__ px, 
     } else if (J.mode == 2) {
       if (s0 > 0.0)
         for (int c = 0; c < cols; ++c) k += snorm[c] > tol * s0;
-    } else if (J.mode == 4) {
+    }
+    if (J.norm_idx >= 0) {
       x.nrm[J.norm_idx] = s0;
       x.scal[J.norm_idx] = s0 > 0.0 ? 1.0 / s0 : 0.0;
     }

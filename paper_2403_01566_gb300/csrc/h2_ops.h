@@ -114,8 +114,9 @@ struct QApplyJob {
 // singular vectors U (rows x cols row-major, column j = u_j, zero for sigma_j=0)
 // if u.arena >= 0, and a rank decision into slot[rank_slot]:
 //   mode 0: none, 1: count(sigma > tol), 2: count(sigma > tol*sigma_0),
-//   4: norm only (writes sigma_0 to nrm[norm_idx] and 1/sigma_0 (0 if
-//   sigma_0 == 0) to scal[norm_idx]).
+//   4: norm only.
+// With norm_idx >= 0 (any mode) it also writes sigma_0 to nrm[norm_idx] and
+// 1/sigma_0 (0 if sigma_0 == 0) to scal[norm_idx].
 // The threshold is tol * scal[tol_idx] (tol alone if tol_idx < 0).
 // A rank above cap sets the error flag (H2_ERANK) and is clamped to cap.
 struct SvdJob {

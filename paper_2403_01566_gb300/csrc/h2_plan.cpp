@@ -1143,6 +1143,11 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     return f;
   };
   std::vector<Factor> agg_result(aggs.size());
+  // Norm slot of each agglomerated block, written by the SVD of its last merge:
+  // the merged block is (Q_c Y_k') Sigma_k' (Q U_k')^T with orthonormal outer
+  // factors, so ||G_b||_2 is that SVD's largest singular value (-1: no merge,
+  // the condensation computes the norm).
+  std::vector<int> agg_nidx(aggs.size(), -1);
   if (!aggs.empty()) {
     // state: per agglomeration, per grid row the accumulated factor
     std::vector<std::vector<Factor>> rowf(aggs.size());
@@ -1338,16 +1343,18 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
         // rho_c above the noise floor (the rest is zero)
         const int gc_rows = J.vertical ? J.f1.rows_t + J.f2.rows_t : J.f1.rows_t;
         const Dim qcols = DS(s.rslot, 0);
+        const bool last = J.vertical && J.row == (1 << aggs[J.agg].d) - 1;
+        const int nidx = last ? (agg_nidx[J.agg] = B.scal()) : -1;
         if (s.two_step) {
           const int qmax = std::min(m1 + m2, gc_rows);
           B.svd_size(qmax, qmax);
           B.sv.push_back(SvdJob{PT(AR_WS, s.R2), PT(AR_WS, s.Y), PT(AR_WS, s.sig), qmax, AGGC, qcols, qcols, 1, 2, J.rel,
-                                PARAM_TOL_AGG, outs[j].m.s, AGGM, -1, NONE()});
+                                PARAM_TOL_AGG, outs[j].m.s, AGGM, nidx, NONE()});
           continue;
         }
         B.svd_size(m1 + m2, std::min(m1 + m2, gc_rows));
         B.sv.push_back(SvdJob{PT(AR_WS, s.rhoc), PT(AR_WS, s.U), PT(AR_WS, s.sig), AGGC, AGGC, wd, qcols, 1, 2, J.rel,
-                              PARAM_TOL_AGG, outs[j].m.s, AGGM, -1, PT(AR_WS, s.piv)});
+                              PARAM_TOL_AGG, outs[j].m.s, AGGM, nidx, PT(AR_WS, s.piv)});
       }
       B.flush_svd(TAG_AGG);
       // two-step jobs: U[:, :k'] = Q2 [Y[:, :k']; 0]
@@ -1402,7 +1409,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   struct Final {
     int cb, t, r;
     Factor f;
-    int nidx;            // norm / scale index
+    int nidx;            // norm / scale index (set already for merged agglomerations)
     int64_t rhoR, rhoL;  // MB x MB row-major
     int64_t Gc, Gcc;     // |t| x MB, |r| x MB
   };
@@ -1410,10 +1417,10 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   for (size_t q = 0; q < V.size(); ++q) {
     const VNode& n = V[q];
     if (n.kind == VK_SU) {
-      Final F{n.cb, n.t, n.r, cell_factor(n), 0, 0, 0, 0, 0};
+      Final F{n.cb, n.t, n.r, cell_factor(n), -1, 0, 0, 0, 0};
       fin.push_back(F);
     } else if (n.kind == VK_AGGROOT) {
-      Final F{n.cb, n.t, n.r, agg_result[n.agg], 0, 0, 0, 0, 0};
+      Final F{n.cb, n.t, n.r, agg_result[n.agg], agg_nidx[n.agg], 0, 0, 0, 0};
       fin.push_back(F);
     }
   }
@@ -1451,9 +1458,11 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
   {
     const int64_t mark = B.ws;
     std::vector<std::array<int64_t, 4>> scr(fin.size());
+    std::vector<char> has_norm(fin.size());
     for (size_t i = 0; i < fin.size(); ++i) {
       Final& F = fin[i];
-      F.nidx = B.scal();
+      has_norm[i] = F.nidx >= 0;
+      if (!has_norm[i]) F.nidx = B.scal();
       F.rhoR = B.alloc((int64_t)MB * MB);
       F.rhoL = B.alloc((int64_t)MB * MB);
       F.Gc = B.alloc((int64_t)F.f.rows_t * MB);
@@ -1486,6 +1495,7 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
       B.tiles(PT(AR_WS, F.Gcc), MB, F.f.rows_r, F.f.m, 0, [&](int r0, int, int c0, Dim) {
         B.term2(rows_of(F.f.R, r0), mref(PT(AR_WS, F.rhoL + (int64_t)c0 * MB), MB, 1), F.f.m.d());
       });
+      if (has_norm[i]) continue;
       nm[i] = B.alloc((int64_t)MB * MB);
       B.tiles(PT(AR_WS, nm[i]), MB, F.f.m.max, F.f.m, 0, [&](int r0, int nr, int c0, Dim) {
         if (F.f.m.s >= 0) {
@@ -1500,6 +1510,10 @@ std::shared_ptr<Plan> make_product_plan(const MatDesc& X, const MatDesc& Y, cons
     B.flush_gemm(TAG_COND);
     for (size_t i = 0; i < fin.size(); ++i) {
       Final& F = fin[i];
+      if (has_norm[i]) {
+        ++P.stats["norms_from_agglomeration"];
+        continue;
+      }
       B.norm(PT(AR_WS, nm[i]), MB, F.f.m, F.nidx);
     }
     B.flush_norm(TAG_COND);

@@ -228,7 +228,7 @@ struct Interp {
     int* rank_out = J.rank_slot >= 0 ? &slot[J.rank_slot] : nullptr;
     if (rows <= 0 || cols <= 0) {
       if (rank_out) *rank_out = 0;
-      if (J.mode == 4) nrm[J.norm_idx] = scal[J.norm_idx] = 0.0;
+      if (J.norm_idx >= 0) nrm[J.norm_idx] = scal[J.norm_idx] = 0.0;
       return;
     }
     const double* S = ptr(J.src);
@@ -295,7 +295,7 @@ struct Interp {
       for (double v : sn) k += v > tol;
     if (J.mode == 2 && s0 > 0.0)
       for (double v : sn) k += v > tol * s0;
-    if (J.mode == 4) {
+    if (J.norm_idx >= 0) {
       nrm[J.norm_idx] = s0;
       scal[J.norm_idx] = s0 > 0.0 ? 1.0 / s0 : 0.0;
     }
