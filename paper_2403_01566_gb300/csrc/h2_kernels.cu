@@ -1060,7 +1060,7 @@ __device__ int householder_cols_la(double* a, int lda, int rows, int cols, doubl
 // columns are pivoted (column of largest remaining norm first, lowest index on
 // ties): cn holds the squared norms of the trailing parts, downdated after each
 // step and recomputed exactly where the downdate has cancelled below 2^-26 of
-// the value at the last recomputation; cn0 holds that value.
+// the value at the last recomputation; cn0 holds 2^-26 times that value.
 //
 // Each step: warp 0 alone picks the pivot, swaps, forms the reflector and
 // scales it (no block barrier inside), then all warps update the trailing
@@ -1084,7 +1084,10 @@ __device__ int householder_cols(double* a, int lda, int rows, int cols, double* 
       double s = 0.0;
       for (int i = lane; i < rows; i += 32) s = fma(cc[i], cc[i], s);
       s = warp_sum(s);
-      if (lane == 0) cn[c] = cn0[c] = s;
+      if (lane == 0) {
+        cn[c] = s;
+        cn0[c] = s * kRecompute;
+      }
     }
     __syncthreads();
     if (floor2 > 0.0 && warp == 0) {
@@ -1190,21 +1193,25 @@ __device__ int householder_cols(double* a, int lda, int rows, int cols, double* 
         }
         for (int o = ts >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
         const double w = t * (cj + p);
+        const double rj = cj - w;  // new row-j entry
         if (c < cols) {
-          if (tl == 0) cc[j] -= w;
+          if (tl == 0) cc[j] = rj;
           for (int i = j + 1 + tl; i < rows; i += ts) cc[i] = fma(-w, col[i], cc[i]);
         }
         if (piv) {
           // downdate the trailing norm by the new row-j entry; recompute on cancellation
-          const double rj = cj - w;
+          // (cn0 >= 0: a negative or -0 downdate reads as a negative integer)
           const double nd = c < cols ? cn[c] - rj * rj : 0.0;
-          const bool need = c < cols && nd <= kRecompute * cn0[c];
+          const bool need = c < cols && __double_as_longlong(nd) <= __double_as_longlong(cn0[c]);
           if (__any_sync(0xffffffffu, need)) {
             double e = 0.0;
             if (need)
               for (int i = j + 1 + tl; i < rows; i += ts) e = fma(cc[i], cc[i], e);
             for (int o = ts >> 1; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-            if (need && tl == 0) cn[c] = cn0[c] = e;
+            if (need && tl == 0) {
+              cn[c] = e;
+              cn0[c] = e * kRecompute;
+            }
           }
           if (c < cols && !need && tl == 0) cn[c] = nd;
         }
@@ -1214,10 +1221,11 @@ __device__ int householder_cols(double* a, int lda, int rows, int cols, double* 
       for (int c = j + 1 + threadIdx.x; c < cols; c += blockDim.x) {
         const double* cc = a + (int64_t)c * lda;
         const double nd = cn[c] - cc[j] * cc[j];
-        if (nd <= kRecompute * cn0[c]) {
+        if (nd <= cn0[c]) {
           double e = 0.0;
           for (int i = j + 1; i < rows; ++i) e = fma(cc[i], cc[i], e);
-          cn[c] = cn0[c] = e;
+          cn[c] = e;
+          cn0[c] = e * kRecompute;
         } else {
           cn[c] = nd;
         }
