@@ -94,6 +94,9 @@ def test_planned_stages_reproduce_the_oracle(interpreter, tmp_path, w, eps):
     if w.dim == 3 and w.order == 4:
         assert stats.get("agg_two_step", 0) > 0
         assert stats.get("qr_truncated", 0) > 0
+    # every agglomerated block takes ||G_b||_2 from the SVD of its last merge
+    # (Section 5.3 weights), not from a norm job of its own
+    assert stats.get("norms_from_agglomeration", 0) == stats.get("agglomerated", 0)
     X, Y = build_pair(w)
     res = O.multiply(X, Y, eps)
     Z = X.dense() @ Y.dense()
