@@ -1,6 +1,7 @@
 """The precision workload at its full size: n = 65536 Fibonacci points on the
 sphere, A = 1/(4 pi |x-y|) (diag 0), leaf 64, eta 2, order 4 (k = 64),
-C = A*A at eps = 1e-4 and 1e-6 (178 GB of workspace on one GB300).
+C = A*A at eps = 1e-4 and 1e-6 (95 GB of product workspace and factors on one
+GB300).
 
 The oracle's own product cannot run at this size (hours, and its recursive
 basis trees), so the GPU's C is checked against the exact product A*A formed
