@@ -129,3 +129,22 @@ def test_svd_sweep_cap_reports_nonconvergence(interpreter, tmp_path):
     err = run_interpreter(interpreter, w, 1e-6, tmp_path, svd_sweeps=1, expect_rc=4)
     assert "interpreter error -5" in err
     run_interpreter(interpreter, w, 1e-6, tmp_path, svd_sweeps=0)
+
+
+@pytest.mark.parametrize("w", [I.plain_1d(256), I.grid_2d(16)], ids=lambda w: w.name)
+def test_planned_exact_product_at_eps0(interpreter, tmp_path, w):
+    """eps = 0 keeps every nonzero singular value: the planned stages give
+    A*B to rounding in every block of the oracle's target block tree."""
+    D, _, _ = run_interpreter(interpreter, w, 0.0, tmp_path, max_rank=64)
+    X, Y = build_pair(w)
+    Z = X.dense() @ Y.dense()
+    assert worst_blockrel(D, Z, Z, O.build_block_tree(X.rows, Y.cols, w.eta)) <= 1e-12
+
+
+def test_planned_single_leaf_tree(interpreter, tmp_path):
+    """n <= leaf size: the root is a leaf and C is one dense block."""
+    w = I.plain_1d(20)
+    D, _, _ = run_interpreter(interpreter, w, 1e-6, tmp_path)
+    X, Y = build_pair(w)
+    Z = X.dense() @ Y.dense()
+    assert np.max(np.abs(D - Z)) <= 1e-13 * np.abs(Z).max()
